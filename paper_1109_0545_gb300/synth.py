@@ -1,0 +1,154 @@
+"""Seeded synthetic inputs shaped like the paper's experiments.
+
+This module draws random sparse polynomial systems, evaluation points and the homotopy
+constant gamma.  It holds none of the method's arithmetic: it only draws numbers, and
+both the CUDA library's tests and the CPU oracle consume what it draws.
+
+Recipe (the paper's own generator is not specified, Sec. 4, 5 and 7 describe only shapes):
+  * the support of a monomial is a uniform random k-subset of {0..n-1}, sorted increasing
+    (the normalised form of Sec. 6);
+  * exponents are uniform integers in [e_lo, e_hi];
+  * coefficients are exp(i theta), theta uniform in [0, 2 pi), leading limb cos/sin in
+    double, lower limbs zero;
+  * points are uniform on the unit torus |x_j| = 1;
+  * gamma is exp(i theta) for one more uniform theta.
+Draw order for one system: for each polynomial, for each monomial: k (if ranged), the
+support, the exponents, theta; then a constant-term theta if requested.  numpy's
+default_rng(seed) generates everything; a family of systems uses default_rng([seed, j])
+for system j, so system j can be drawn without the others.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class System:
+    """A sparse polynomial system in the CSR form the library's loader takes."""
+    n: int
+    npoly: int
+    mon_ptr: np.ndarray  # int32 [npoly+1]
+    var_ptr: np.ndarray  # int32 [nmon+1]
+    var_idx: np.ndarray  # int32 [nvar]
+    var_exp: np.ndarray  # int32 [nvar]
+    coef: np.ndarray     # complex128 [nmon], leading limbs (lower limbs are zero)
+
+    @property
+    def nmon(self) -> int:
+        return int(self.mon_ptr[-1])
+
+    @property
+    def nvar(self) -> int:
+        return int(self.var_ptr[-1])
+
+    def as_dict(self) -> dict:
+        return {"n": self.n, "npoly": self.npoly, "mon_ptr": self.mon_ptr,
+                "var_ptr": self.var_ptr, "var_idx": self.var_idx, "var_exp": self.var_exp}
+
+    def coef_limbs(self, L: int) -> np.ndarray:
+        """coef[m][2][L]: re limbs then im limbs, leading limb first."""
+        return limbs(self.coef, L)
+
+
+def limbs(z: np.ndarray, L: int) -> np.ndarray:
+    """Complex doubles -> [..., 2, L] with the lower limbs zero."""
+    z = np.asarray(z, dtype=np.complex128)
+    out = np.zeros(z.shape + (2, L), dtype=np.float64)
+    out[..., 0, 0] = z.real
+    out[..., 1, 0] = z.imag
+    return out
+
+
+def _draw(rng, v):
+    if isinstance(v, tuple):
+        return int(rng.integers(v[0], v[1] + 1))
+    return int(v)
+
+
+def random_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
+                  const_term: bool = False, npoly: int | None = None) -> System:
+    """One random system.  mons_per_poly and k are ints or inclusive (lo, hi) ranges,
+    exps is an inclusive (lo, hi) range."""
+    npoly = n if npoly is None else npoly
+    mon_ptr = [0]
+    var_ptr = [0]
+    idx: list[np.ndarray] = []
+    ex: list[np.ndarray] = []
+    thetas: list[float] = []
+    for _ in range(npoly):
+        m_i = _draw(rng, mons_per_poly)
+        for _ in range(m_i):
+            kk = _draw(rng, k)
+            sup = np.sort(rng.choice(n, size=kk, replace=False)).astype(np.int32)
+            e = rng.integers(exps[0], exps[1] + 1, size=kk).astype(np.int32)
+            idx.append(sup)
+            ex.append(e)
+            var_ptr.append(var_ptr[-1] + kk)
+            thetas.append(rng.uniform(0.0, 2.0 * np.pi))
+        cnt = m_i
+        if const_term:
+            var_ptr.append(var_ptr[-1])
+            thetas.append(rng.uniform(0.0, 2.0 * np.pi))
+            cnt += 1
+        mon_ptr.append(mon_ptr[-1] + cnt)
+    th = np.array(thetas)
+    return System(n=n, npoly=npoly,
+                  mon_ptr=np.array(mon_ptr, dtype=np.int32),
+                  var_ptr=np.array(var_ptr, dtype=np.int32),
+                  var_idx=np.concatenate(idx).astype(np.int32) if idx else np.zeros(0, np.int32),
+                  var_exp=np.concatenate(ex).astype(np.int32) if ex else np.zeros(0, np.int32),
+                  coef=np.cos(th) + 1j * np.sin(th))
+
+
+def torus_points(rng: np.random.Generator, npts: int, n: int) -> np.ndarray:
+    """npts points uniform on the unit torus, complex128 [npts][n]."""
+    th = rng.uniform(0.0, 2.0 * np.pi, size=(npts, n))
+    return np.cos(th) + 1j * np.sin(th)
+
+
+def unit_complex(rng: np.random.Generator) -> complex:
+    th = rng.uniform(0.0, 2.0 * np.pi)
+    return complex(np.cos(th), np.sin(th))
+
+
+# ---------------------------------------------------------------------------------------
+# The workloads.  Each returns plain data; sizes can be reduced for tests.
+# ---------------------------------------------------------------------------------------
+
+def single_path_dd(seed: int = 1):
+    """One path, complex DD: n = 8, 8 polynomials of 12 monomials plus a constant term,
+    3 distinct variables per monomial, exponents in {1,2,3}.  Returns (system, gamma)."""
+    rng = np.random.default_rng(seed)
+    s = random_system(rng, 8, 12, 3, (1, 3), const_term=True)
+    return s, unit_complex(rng)
+
+
+def eval_throughput(seed: int = 2, npts: int = 65536, n: int = 32, mons: int = 128,
+                    k: int = 6, exps=(1, 4)):
+    """Eval+Jacobian throughput workload: n = 32, 32 x 128 monomials, k = 6, exponents
+    in {1..4}; npts points on the unit torus.  Returns (system, points, gamma)."""
+    rng = np.random.default_rng(seed)
+    s = random_system(rng, n, mons, k, exps)
+    gamma = unit_complex(rng)
+    pts = torus_points(rng, npts, n)
+    return s, pts, gamma
+
+
+def uneven_path_system(seed: int, j: int):
+    """System j of the batched uneven-path family: n in {10..64}, monomials per
+    polynomial in {20..200}, variables per monomial in {2..8}, exponents in {1..3}.
+    Returns (system, gamma)."""
+    rng = np.random.default_rng([seed, j])
+    n = int(rng.integers(10, 65))
+    s = random_system(rng, n, (20, 200), (2, 8), (1, 3))
+    return s, unit_complex(rng)
+
+
+def large_path_qd(seed: int = 4, n: int = 96, mons: int = 1024, k: int = 12, exps=(1, 5)):
+    """Large single path, complex QD: n = 96, 96 x 1024 monomials, k = 12, exponents in
+    {1..5}.  Returns (system, gamma)."""
+    rng = np.random.default_rng(seed)
+    s = random_system(rng, n, mons, k, exps)
+    return s, unit_complex(rng)
