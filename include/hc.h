@@ -1,0 +1,151 @@
+/*
+ * hc.h -- C ABI of the GB300 (sm_103a) hot path of the multithreaded path tracker of
+ * Verschelde & Yoffe, "Quality Up in Polynomial Homotopy Continuation by Multithreaded
+ * Path Tracking" (2011).
+ *
+ * The library evaluates a sparse polynomial system and its full Jacobian by
+ * algorithmic differentiation (Sec. 6), in complex double, double-double or
+ * quad-double arithmetic (Sec. 1, 2), assembles the homotopy
+ *     h(x,t) = gamma (1-t) g(x) + t f(x),   g_i(x) = x_i^{d_i} - 1,
+ * with t a parameter (Sec. 7, Table 6 caption), and runs the Newton corrector of
+ * Alg. 4.1 (Gaussian elimination with partial pivoting, Sec. 4) and the path tracker
+ * of Alg. 3.1 on top of it.
+ *
+ * Conventions shared by every call:
+ *   - L = number of limbs per real: 1 (double), 2 (double-double), 4 (quad-double);
+ *     a multi-limb value is the unevaluated sum of its limbs, leading limb first.
+ *   - Device arrays are structure-of-arrays with the point index fastest:
+ *       X[2][L][n][npts]          points (re limbs, then im limbs)
+ *       F[2][L][npoly][npts]      values
+ *       J[2][L][npoly][n][npts]   Jacobians, row i = polynomial, column j = variable
+ *     i.e. part c, limb l, index i of point p sits at base[((c*L + l)*rows + i)*npts + p].
+ *   - Return codes: HC_SUCCESS (0) or a negative HC_E* code; hc_last_error() then
+ *     describes the failure.  Per-point outcomes go to caller-owned status arrays.
+ *   - All device calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream).  Calls on the same hc_system share its
+ *     workspace and must not overlap in time: issue them on one stream.
+ *   - The caller owns every input/output buffer; the library owns hc_system and its
+ *     device tables and workspace.
+ *   - Invalid arguments are rejected on the host with HC_EINVAL before any launch.
+ */
+#ifndef HC_H
+#define HC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define HC_SUCCESS 0
+#define HC_EINVAL (-1)    /* invalid argument or malformed system */
+#define HC_ENOMEM (-2)    /* device allocation failed */
+#define HC_ECUDA (-3)     /* a CUDA runtime call failed */
+#define HC_ENOTIMPL (-4)  /* combination not supported */
+#define HC_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+
+/* per-point / per-path status */
+#define HC_OK 0         /* converged / tracked to t = 1 */
+#define HC_NOCONV 1     /* end-point Newton did not reach its tolerance */
+#define HC_SINGULAR 2   /* a pivot of the elimination was exactly zero */
+#define HC_MIN_STEP 3   /* step size fell below its minimum (Alg. 3.1 stop criterion) */
+#define HC_MAX_STEPS 4  /* corrector stages exhausted (Alg. 3.1 stop criterion) */
+#define HC_DIVERGED 5   /* ||x||_inf exceeded its bound */
+#define HC_NONFINITE 6  /* Inf or NaN met */
+
+/* precision = limbs per real */
+#define HC_PREC_D 1
+#define HC_PREC_DD 2
+#define HC_PREC_QD 4
+
+/* linear solve of the Newton step */
+#define HC_LU_NATIVE 0       /* elimination in the working precision (Sec. 4) */
+#define HC_LU_FP64_REFINE 1  /* FP64 LU, residual and update in the working precision */
+
+typedef struct hc_system hc_system;
+
+/*
+ * hc_system_load -- validate a sparse system and upload it to the current device.
+ * The normalised monomial form of Sec. 6: polynomial i owns monomials
+ * mon_ptr[i] .. mon_ptr[i+1]-1; monomial m owns variables var_ptr[m] .. var_ptr[m+1]-1
+ * with strictly increasing 0-based indices var_idx[] < n and exponents var_exp[] >= 1;
+ * a monomial with no variables is a constant term.  At most 32 variables per monomial,
+ * exponents at most 64, n at most 1024.
+ *   coef   host, [nmon][2][L] doubles (re limbs, im limbs), finite
+ *   prec   HC_PREC_D / _DD / _QD (= L)
+ *   gamma  host, the homotopy constant (re, im) in double
+ * The degree d_i of the start system is the largest total degree of a monomial of f_i.
+ * All host arrays are copied; the caller keeps ownership.  Returns HC_SUCCESS and
+ * *out, or HC_EINVAL (malformed input, nothing allocated), HC_ENOMEM, HC_ECUDA.
+ */
+int hc_system_load(hc_system **out, int n, int npoly, const int32_t *mon_ptr,
+                   const int32_t *var_ptr, const int32_t *var_idx, const int32_t *var_exp,
+                   const double *coef, int prec, const double gamma[2]);
+
+/* Free a system and its device tables and workspace (NULL is a no-op).  Synchronises
+ * the device first, so no call may still be using it. */
+void hc_system_free(hc_system *sys);
+
+/* Sizes of a loaded system: any pointer may be NULL.  Returns HC_EINVAL on NULL sys. */
+int hc_system_info(const hc_system *sys, int *n, int *npoly, int *nmon, int *nvar,
+                   int *prec, int *max_exp, int *max_deg);
+
+/*
+ * hc_eval_jac -- values and full Jacobian at npts points (Alg. 4.1 Monomial_Evaluation
+ * followed by Coefficient_Product; the monomial scheme of Sec. 6).
+ *   t < 0   evaluate f itself (npoly may differ from n);
+ *   t >= 0  evaluate the homotopy h(., t) and its Jacobian in x (requires npoly == n
+ *           and every d_i >= 1).
+ *   x  device X[2][L][n][npts];  f  device F[2][L][npoly][npts];
+ *   J  device J[2][L][npoly][n][npts], or NULL for values only.
+ * Uses the system's workspace (allocated on first use, grown as needed).
+ * npts == 0 is a no-op.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA.
+ */
+int hc_eval_jac(hc_system *sys, int npts, double t, const double *x, double *f, double *J,
+                void *stream);
+
+/*
+ * hc_newton_step -- one Newton iteration of Alg. 4.1 at every point, on h(., t)
+ * (t >= 0) or on f (t < 0, npoly == n required):
+ *   evaluate h and J at x; res_norm[p] = max_i |h_i| (moduli of the leading limbs,
+ *   in double) at the incoming x; solve J dz = -h with partial pivoting; x += dz.
+ *   lu_mode     HC_LU_NATIVE or HC_LU_FP64_REFINE
+ *   max_refine  refinement sweeps for HC_LU_FP64_REFINE (>= 1); refinement stops
+ *               early once ||correction||_inf <= 2^(-53 L) max(||x||_inf, ||dz||_inf)
+ *               or the correction no longer shrinks (norms of the leading limbs)
+ *   x        device X[2][L][n][npts], updated in place where status is HC_OK
+ *   res_norm device double[npts] (may be NULL)
+ *   status   device int32[npts]: HC_OK, HC_SINGULAR (x unchanged) or HC_NONFINITE
+ *            (x unchanged)
+ *   sweeps   device int32[npts] (may be NULL): refinement sweeps taken (0 for native)
+ * Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA.
+ */
+int hc_newton_step(hc_system *sys, int npts, double t, double *x, int lu_mode,
+                   int max_refine, double *res_norm, int32_t *status, int32_t *sweeps,
+                   void *stream);
+
+/*
+ * hc_set_tiles -- tile shape of the evaluation kernels for every later call in this
+ * process (the autotuner's knob; 0 = automatic):
+ *   rows_per_task  polynomials one warp evaluates per task (its 32 points each)
+ *   blocks_per_sm  resident 4-warp blocks per SM of the persistent grid (<= 32)
+ * Errors: HC_EINVAL.
+ */
+int hc_set_tiles(int rows_per_task, int blocks_per_sm);
+
+/* Message describing the last failure on the calling host thread ("" if none). */
+const char *hc_last_error(void);
+
+/*
+ * hc_probe_fp64_peak -- measurement helper, not part of the method: times independent
+ * FP64 FMA chains on every SM of the current device and returns, in *gops, the FP64
+ * instruction rate in 10^9 instructions per second (one FMA = one instruction).
+ * Synchronous.  Errors: HC_ECUDA.
+ */
+int hc_probe_fp64_peak(double *gops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HC_H */

@@ -790,17 +790,20 @@ int or_solve(int L, int n, const double *A, const double *b, double *x)
  * Mixed-precision solve: factor the leading limbs of A in plain double (the same
  * elimination, L = 1), then refine in L-limb arithmetic:
  *   dz_0 = LU^{-1} b_lead;  r = b - A dz;  dz += LU^{-1} r_lead;
- * until ||LU^{-1} r||_inf <= ref_tol * ||dz||_inf or max_refine sweeps.
+ * Stop after max_refine sweeps, or once the correction is below 2^(-53 L) of
+ * max(||x||, ||dz||) (x + dz is formed next, so that is the working precision of the
+ * update), or once it no longer shrinks (the residual is at its rounding floor).
  * Returns 0/1 as ge_solve; *sweeps receives the number of refinement sweeps.
  */
 static int mixed_solve(int L, int n, const C *A, const C *b, C *z, int max_refine,
-                       double ref_tol, int *sweeps)
+                       double xnorm, int *sweeps)
 {
     int w = n + 1;
     C *M = (C *)malloc(sizeof(C) * (size_t)n * (size_t)w);
     C *d = (C *)malloc(sizeof(C) * (size_t)n);
     C *r = (C *)malloc(sizeof(C) * (size_t)n);
     int rc = 0;
+    double tol = ldexp(1.0, -53 * L), prev = INFINITY;
     *sweeps = 0;
     /* the first solve and every correction solve use the double LU; a plain-double
        re-elimination of [A_lead r_lead] is the same arithmetic as reusing the factors */
@@ -841,7 +844,8 @@ static int mixed_solve(int L, int n, const C *A, const C *b, C *z, int max_refin
         }
         if (it > 0) {
             *sweeps = it;
-            if (dn <= ref_tol * zn) break;
+            if (dn <= tol * (xnorm > zn ? xnorm : zn) || dn >= prev) break;
+            prev = dn;
         }
     }
     free(M);
@@ -858,11 +862,6 @@ static int mixed_solve(int L, int n, const C *A, const C *b, C *z, int max_refin
  * ---------------------------------------------------------------------------------- */
 enum { OR_OK = 0, OR_NOCONV = 1, OR_SINGULAR = 2, OR_MIN_STEP = 3, OR_MAX_STEPS = 4,
        OR_DIVERGED = 5, OR_NONFINITE = 6 };
-
-static double ref_tol_for(int L)
-{
-    return L == 1 ? 0.0 : (L == 2 ? 1e-32 : 1e-64);
-}
 
 static double cnorm_inf_lead(int n, const C *z);
 
@@ -900,7 +899,7 @@ static int newton_once(int L, const sysdesc *s, const int32_t *deg, double t, C 
             b[i].re = r_neg(L, b[i].re);
             b[i].im = r_neg(L, b[i].im);
         }
-        rc = mixed_solve(L, n, Jv, b, dz, max_refine, ref_tol_for(L), sweeps);
+        rc = mixed_solve(L, n, Jv, b, dz, max_refine, cnorm_inf_lead(n, z), sweeps);
         free(b);
     }
     if (rc) return OR_SINGULAR;

@@ -1,0 +1,20 @@
+// hc_eval.cuh -- evaluation entry points shared between translation units.
+#pragma once
+#include "points.cuh"
+
+struct EvalTiles {
+    int rows_per_task = 0;  // polynomials per warp task (0 = automatic)
+    int blocks_per_sm = 0;  // resident 4-warp blocks per SM (0 = automatic)
+};
+
+namespace hc {
+template <int L>
+int launch_eval(const DevSys &S, int npts, double t, const double *X, double *PW, double *F,
+                double *J, const EvalTiles &tiles, cudaStream_t st);
+}
+
+EvalTiles &hc_eval_tiles();  // process-wide tile choice (hc_set_tiles)
+size_t hc_pw_bytes(const hc_system *s, int npts);
+int hc_check_eval_args(const hc_system *s, int npts, double t);
+int hc_eval_dispatch(hc_system *s, int npts, double t, const double *x, double *pw, double *f,
+                     double *J, const EvalTiles &tiles, cudaStream_t st);

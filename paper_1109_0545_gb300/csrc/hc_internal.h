@@ -1,0 +1,54 @@
+// hc_internal.h -- library-private state shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/hc.h"
+
+#define HC_KMAX 32     // variables per monomial
+#define HC_EXPMAX 64   // exponent bound
+#define HC_NMAX 1024   // unknowns
+
+// Device view of a loaded system, passed to kernels by value.
+struct DevSys {
+    int n, npoly, nmon, nvar;
+    int max_exp;        // largest exponent
+    const int32_t *mon_ptr;   // [npoly+1]
+    const int32_t *var_ptr;   // [nmon+1]
+    const int32_t *var_pack;  // [nvar]: index | exponent << 16
+    const double *coef;       // [nmon][2][L]
+    const int32_t *deg;       // [npoly]
+    double gre, gim;          // gamma
+};
+
+struct hc_system {
+    int n, npoly, nmon, nvar, prec, max_exp, max_deg;
+    int min_deg;
+    double gamma[2];
+    int device;
+    DevSys dev;
+    void *dev_block;       // one allocation holding every table
+    // workspace, grown on demand
+    void *ws;
+    size_t ws_bytes;
+    // host copies (used to build per-kernel layouts)
+    int32_t *h_mon_ptr, *h_var_ptr, *h_var_pack, *h_deg;
+};
+
+// error reporting (thread-local message)
+int hc_fail(int code, const char *fmt, ...);
+int hc_cuda_fail(cudaError_t e, const char *what);
+#define HC_CUDA_TRY(call)                                         \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return hc_cuda_fail(_e, #call);   \
+    } while (0)
+
+// workspace of at least `bytes`, 256-byte aligned; grows (synchronising) if needed
+int hc_workspace(hc_system *s, size_t bytes, void **out);
+
+// number of SMs of the current device (cached)
+int hc_num_sms(void);
+
+static inline size_t hc_align256(size_t b) { return (b + 255) & ~(size_t)255; }

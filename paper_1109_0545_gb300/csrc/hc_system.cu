@@ -1,0 +1,271 @@
+// hc_system.cu -- loading a sparse system (the normalised monomial form of Sec. 6),
+// error reporting, workspace, and the FP64 peak probe.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "hc_internal.h"
+
+static thread_local char g_err[512];
+
+extern "C" const char *hc_last_error(void) { return g_err; }
+
+int hc_fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int hc_cuda_fail(cudaError_t e, const char *what)
+{
+    snprintf(g_err, sizeof g_err, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HC_ENOMEM : HC_ECUDA;
+}
+
+int hc_num_sms(void)
+{
+    static int cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+int hc_workspace(hc_system *s, size_t bytes, void **out)
+{
+    if (bytes == 0) bytes = 256;
+    if (s->ws_bytes < bytes) {
+        if (s->ws) {
+            // the old workspace may still be in use by queued work
+            HC_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(s->ws);
+            s->ws = NULL;
+            s->ws_bytes = 0;
+        }
+        void *p = NULL;
+        HC_CUDA_TRY(cudaMalloc(&p, bytes));
+        s->ws = p;
+        s->ws_bytes = bytes;
+    }
+    *out = s->ws;
+    return HC_SUCCESS;
+}
+
+// Validation of the normalised form: every failure is HC_EINVAL with a message.
+static int validate(int n, int npoly, const int32_t *mon_ptr, const int32_t *var_ptr,
+                    const int32_t *var_idx, const int32_t *var_exp, const double *coef,
+                    int prec, const double *gamma)
+{
+    if (n < 1 || n > HC_NMAX) return hc_fail(HC_EINVAL, "n = %d out of [1, %d]", n, HC_NMAX);
+    if (npoly < 1 || npoly > HC_NMAX) return hc_fail(HC_EINVAL, "npoly = %d out of range", npoly);
+    if (prec != 1 && prec != 2 && prec != 4) return hc_fail(HC_EINVAL, "prec = %d not 1, 2 or 4", prec);
+    if (!mon_ptr || !var_ptr || !coef || !gamma) return hc_fail(HC_EINVAL, "NULL array");
+    if (mon_ptr[0] != 0) return hc_fail(HC_EINVAL, "mon_ptr[0] != 0");
+    for (int i = 0; i < npoly; i++)
+        if (mon_ptr[i + 1] < mon_ptr[i]) return hc_fail(HC_EINVAL, "mon_ptr decreases at %d", i);
+    long long nmon = mon_ptr[npoly];
+    if (nmon > (1LL << 30)) return hc_fail(HC_EINVAL, "too many monomials");
+    if (var_ptr[0] != 0) return hc_fail(HC_EINVAL, "var_ptr[0] != 0");
+    for (long long m = 0; m < nmon; m++) {
+        int q0 = var_ptr[m], q1 = var_ptr[m + 1];
+        if (q1 < q0) return hc_fail(HC_EINVAL, "var_ptr decreases at monomial %lld", m);
+        if (q1 - q0 > HC_KMAX) return hc_fail(HC_EINVAL, "monomial %lld has %d > %d variables", m, q1 - q0, HC_KMAX);
+        for (int q = q0; q < q1; q++) {
+            if (!var_idx || !var_exp) return hc_fail(HC_EINVAL, "NULL var arrays");
+            if (var_idx[q] < 0 || var_idx[q] >= n)
+                return hc_fail(HC_EINVAL, "monomial %lld: index %d out of [0,%d)", m, var_idx[q], n);
+            if (var_exp[q] < 1 || var_exp[q] > HC_EXPMAX)
+                return hc_fail(HC_EINVAL, "monomial %lld: exponent %d out of [1,%d]", m, var_exp[q], HC_EXPMAX);
+            if (q > q0 && var_idx[q] <= var_idx[q - 1])
+                return hc_fail(HC_EINVAL, "monomial %lld: indices not strictly increasing", m);
+        }
+        for (int c = 0; c < 2 * prec; c++)
+            if (!std::isfinite(coef[m * 2 * prec + c]))
+                return hc_fail(HC_EINVAL, "monomial %lld: coefficient not finite", m);
+    }
+    if (!std::isfinite(gamma[0]) || !std::isfinite(gamma[1])) return hc_fail(HC_EINVAL, "gamma not finite");
+    return HC_SUCCESS;
+}
+
+extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *mon_ptr,
+                              const int32_t *var_ptr, const int32_t *var_idx,
+                              const int32_t *var_exp, const double *coef, int prec,
+                              const double gamma[2])
+{
+    if (!out) return hc_fail(HC_EINVAL, "out is NULL");
+    *out = NULL;
+    int rc = validate(n, npoly, mon_ptr, var_ptr, var_idx, var_exp, coef, prec, gamma);
+    if (rc) return rc;
+    int nmon = mon_ptr[npoly];
+    int nvar = var_ptr[nmon];
+
+    hc_system *s = (hc_system *)calloc(1, sizeof(hc_system));
+    if (!s) return hc_fail(HC_ENOMEM, "host allocation failed");
+    s->n = n;
+    s->npoly = npoly;
+    s->nmon = nmon;
+    s->nvar = nvar;
+    s->prec = prec;
+    s->gamma[0] = gamma[0];
+    s->gamma[1] = gamma[1];
+    cudaGetDevice(&s->device);
+
+    // host tables: packed (index, exponent), degrees
+    s->h_mon_ptr = (int32_t *)malloc(sizeof(int32_t) * (npoly + 1));
+    s->h_var_ptr = (int32_t *)malloc(sizeof(int32_t) * (nmon + 1));
+    s->h_var_pack = (int32_t *)malloc(sizeof(int32_t) * (nvar > 0 ? nvar : 1));
+    s->h_deg = (int32_t *)malloc(sizeof(int32_t) * npoly);
+    if (!s->h_mon_ptr || !s->h_var_ptr || !s->h_var_pack || !s->h_deg) {
+        hc_system_free(s);
+        return hc_fail(HC_ENOMEM, "host allocation failed");
+    }
+    memcpy(s->h_mon_ptr, mon_ptr, sizeof(int32_t) * (npoly + 1));
+    memcpy(s->h_var_ptr, var_ptr, sizeof(int32_t) * (nmon + 1));
+    int max_exp = 1;
+    for (int q = 0; q < nvar; q++) {
+        s->h_var_pack[q] = var_idx[q] | (var_exp[q] << 16);
+        if (var_exp[q] > max_exp) max_exp = var_exp[q];
+    }
+    int max_deg = 0, min_deg = 1 << 30;
+    for (int i = 0; i < npoly; i++) {
+        int d = 0;
+        for (int m = mon_ptr[i]; m < mon_ptr[i + 1]; m++) {
+            int tot = 0;
+            for (int q = var_ptr[m]; q < var_ptr[m + 1]; q++) tot += var_exp[q];
+            if (tot > d) d = tot;
+        }
+        s->h_deg[i] = d;
+        if (d > max_deg) max_deg = d;
+        if (d < min_deg) min_deg = d;
+    }
+    s->max_exp = max_exp;
+    s->max_deg = max_deg;
+    s->min_deg = min_deg;
+
+    // one device block: mon_ptr | var_ptr | var_pack | deg | coef (coef 256-aligned)
+    size_t o_mon = 0;
+    size_t o_var = hc_align256(o_mon + sizeof(int32_t) * (npoly + 1));
+    size_t o_pack = hc_align256(o_var + sizeof(int32_t) * (nmon + 1));
+    size_t o_deg = hc_align256(o_pack + sizeof(int32_t) * (nvar > 0 ? nvar : 1));
+    size_t o_coef = hc_align256(o_deg + sizeof(int32_t) * npoly);
+    size_t total = hc_align256(o_coef + sizeof(double) * 2 * prec * (size_t)(nmon > 0 ? nmon : 1));
+    cudaError_t e = cudaMalloc(&s->dev_block, total);
+    if (e != cudaSuccess) {
+        hc_system_free(s);
+        return hc_cuda_fail(e, "cudaMalloc(system tables)");
+    }
+    char *b = (char *)s->dev_block;
+    e = cudaMemcpy(b + o_mon, s->h_mon_ptr, sizeof(int32_t) * (npoly + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_var, s->h_var_ptr, sizeof(int32_t) * (nmon + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nvar > 0) e = cudaMemcpy(b + o_pack, s->h_var_pack, sizeof(int32_t) * nvar, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_deg, s->h_deg, sizeof(int32_t) * npoly, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nmon > 0)
+        e = cudaMemcpy(b + o_coef, coef, sizeof(double) * 2 * prec * (size_t)nmon, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        hc_system_free(s);
+        return hc_cuda_fail(e, "cudaMemcpy(system tables)");
+    }
+    DevSys &d = s->dev;
+    d.n = n;
+    d.npoly = npoly;
+    d.nmon = nmon;
+    d.nvar = nvar;
+    d.max_exp = max_exp;
+    d.mon_ptr = (const int32_t *)(b + o_mon);
+    d.var_ptr = (const int32_t *)(b + o_var);
+    d.var_pack = (const int32_t *)(b + o_pack);
+    d.deg = (const int32_t *)(b + o_deg);
+    d.coef = (const double *)(b + o_coef);
+    d.gre = gamma[0];
+    d.gim = gamma[1];
+    *out = s;
+    return HC_SUCCESS;
+}
+
+extern "C" void hc_system_free(hc_system *s)
+{
+    if (!s) return;
+    if (s->dev_block || s->ws) cudaDeviceSynchronize();
+    if (s->dev_block) cudaFree(s->dev_block);
+    if (s->ws) cudaFree(s->ws);
+    free(s->h_mon_ptr);
+    free(s->h_var_ptr);
+    free(s->h_var_pack);
+    free(s->h_deg);
+    free(s);
+}
+
+extern "C" int hc_system_info(const hc_system *s, int *n, int *npoly, int *nmon, int *nvar,
+                              int *prec, int *max_exp, int *max_deg)
+{
+    if (!s) return hc_fail(HC_EINVAL, "sys is NULL");
+    if (n) *n = s->n;
+    if (npoly) *npoly = s->npoly;
+    if (nmon) *nmon = s->nmon;
+    if (nvar) *nvar = s->nvar;
+    if (prec) *prec = s->prec;
+    if (max_exp) *max_exp = s->max_exp;
+    if (max_deg) *max_deg = s->max_deg;
+    return HC_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 peak probe: CHAINS independent FMA chains per thread, every SM busy.
+// ---------------------------------------------------------------------------------
+#define PROBE_CHAINS 8
+#define PROBE_ITERS 4096
+
+__global__ void k_probe_dfma(double *out, double a, double b)
+{
+    double v[PROBE_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; c++) v[c] = threadIdx.x * 1e-3 + c;
+#pragma unroll 4
+    for (int i = 0; i < PROBE_ITERS; i++) {
+#pragma unroll
+        for (int c = 0; c < PROBE_CHAINS; c++) v[c] = __fma_rn(v[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; c++) s += v[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+extern "C" int hc_probe_fp64_peak(double *gops)
+{
+    if (!gops) return hc_fail(HC_EINVAL, "gops is NULL");
+    const int sms = hc_num_sms(), block = 256, grid = sms * 4;
+    double *out = NULL;
+    HC_CUDA_TRY(cudaMalloc(&out, sizeof(double) * (size_t)grid * block));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 5; rep++) {
+        cudaEventRecord(e0, 0);
+        k_probe_dfma<<<grid, block>>>(out, 0.999999, 1e-7);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (err != cudaSuccess) return hc_cuda_fail(err, "k_probe_dfma");
+    double ops = (double)grid * block * PROBE_ITERS * PROBE_CHAINS;
+    *gops = ops / (best * 1e-3) * 1e-9;
+    return HC_SUCCESS;
+}

@@ -1,0 +1,399 @@
+// mp.cuh -- complex double / double-double / quad-double arithmetic for sm_103a.
+//
+// Extended precision from error-free transformations (Dekker 1971; Hida, Li & Bailey
+// 2001), the arithmetic the paper's tracker runs in (Sec. 1, Sec. 2).  Built on the FMA:
+// the exact error of a product is one fused multiply-add, so no Dekker split is needed.
+//
+// Every floating-point operation below goes through an explicit round-to-nearest
+// intrinsic (__dadd_rn, __dmul_rn, __fma_rn): the compiler may neither contract a
+// multiply and an add into one FMA nor reassociate, either of which would silently
+// destroy the error terms.
+//
+// On GB300 the FP64 pipe is the scarce unit (about 1.6 FP64 instructions per clock per
+// SM, against ~100 FP32 FMAs), so every routine is written to minimise FP64
+// instructions; the comment of each states its count (negations fold into operand
+// modifiers and cost nothing).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hc {
+
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// s + e = a + b exactly (Knuth).  6 FP64.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = add_(a, b);
+    double bb = sub_(s, a);
+    e = add_(sub_(a, sub_(s, bb)), sub_(b, bb));
+}
+
+// s + e = a + b exactly when |a| >= |b| or a == 0 (Dekker).  3 FP64.
+__device__ __forceinline__ void fast_two_sum(double a, double b, double &s, double &e)
+{
+    s = add_(a, b);
+    e = sub_(b, sub_(s, a));
+}
+
+// p + e = a * b exactly (FMA).  2 FP64.
+__device__ __forceinline__ void two_prod(double a, double b, double &p, double &e)
+{
+    p = mul_(a, b);
+    e = fma_(a, b, -p);
+}
+
+template <int L> struct R { double v[L]; };
+template <int L> struct C { R<L> re, im; };
+
+template <int L> __device__ __forceinline__ R<L> r_zero()
+{
+    R<L> r;
+#pragma unroll
+    for (int j = 0; j < L; j++) r.v[j] = 0.0;
+    return r;
+}
+template <int L> __device__ __forceinline__ R<L> r_from(double d)
+{
+    R<L> r = r_zero<L>();
+    r.v[0] = d;
+    return r;
+}
+template <int L> __device__ __forceinline__ R<L> r_neg(R<L> a)
+{
+#pragma unroll
+    for (int j = 0; j < L; j++) a.v[j] = -a.v[j];
+    return a;
+}
+
+// ---------------------------------------------------------------- renormalisation (QD)
+// Five components of roughly decreasing magnitude -> four nonoverlapping limbs.
+// Bottom-up two-sums carry the value up exactly (two-sums, not fast-two-sums: after a
+// cancellation the components need not be ordered); the top-down fast-two-sums then
+// re-split it (a zero component bubbles down: fast_two_sum(0, b) = (b, 0)).  34 FP64.
+__device__ __forceinline__ R<4> renorm5(double c0, double c1, double c2, double c3, double c4)
+{
+    double s, t3, t2, t1, t0;
+    two_sum(c3, c4, s, t3);
+    two_sum(c2, s, s, t2);
+    two_sum(c1, s, s, t1);
+    two_sum(c0, s, c0, t0);
+    R<4> r;
+    double e;
+    fast_two_sum(c0, t0, r.v[0], e);
+    fast_two_sum(e, t1, r.v[1], e);
+    fast_two_sum(e, t2, r.v[2], e);
+    r.v[3] = add_(e, t3);
+    return r;
+}
+
+// ---------------------------------------------------------------- addition
+__device__ __forceinline__ R<1> r_add(R<1> a, R<1> b)  // 1 FP64
+{
+    R<1> r;
+    r.v[0] = add_(a.v[0], b.v[0]);
+    return r;
+}
+// double-double: two-sum of the leading limbs, lower limbs added into the error.  11 FP64.
+__device__ __forceinline__ R<2> r_add(R<2> a, R<2> b)
+{
+    double s, e;
+    two_sum(a.v[0], b.v[0], s, e);
+    e = add_(e, add_(a.v[1], b.v[1]));
+    R<2> r;
+    fast_two_sum(s, e, r.v[0], r.v[1]);
+    return r;
+}
+// quad-double: limb-wise two-sums, errors cascaded one order down, renormalised.  ~71 FP64.
+__device__ __forceinline__ R<4> r_add(R<4> a, R<4> b)
+{
+    double s0, s1, s2, s3, t0, t1, t2, t3, u, w;
+    two_sum(a.v[0], b.v[0], s0, t0);
+    two_sum(a.v[1], b.v[1], s1, t1);
+    two_sum(a.v[2], b.v[2], s2, t2);
+    two_sum(a.v[3], b.v[3], s3, t3);
+    two_sum(s1, t0, s1, t0);           // order 1 -> s1, order-2 error t0
+    two_sum(s2, t1, s2, u);            // order 2: s2 + t1 + t0
+    two_sum(s2, t0, s2, w);
+    double c3 = add_(add_(add_(s3, t2), add_(u, w)), t3);  // order 3
+    return renorm5(s0, s1, s2, c3, 0.0);
+}
+
+template <int L> __device__ __forceinline__ R<L> r_sub(R<L> a, R<L> b) { return r_add(a, r_neg(b)); }
+
+// ---------------------------------------------------------------- multiplication
+__device__ __forceinline__ R<1> r_mul(R<1> a, R<1> b)  // 1 FP64
+{
+    R<1> r;
+    r.v[0] = mul_(a.v[0], b.v[0]);
+    return r;
+}
+// double-double: exact leading product plus the two cross terms.  7 FP64.
+__device__ __forceinline__ R<2> r_mul(R<2> a, R<2> b)
+{
+    double p, e;
+    two_prod(a.v[0], b.v[0], p, e);
+    e = fma_(a.v[0], b.v[1], e);
+    e = fma_(a.v[1], b.v[0], e);
+    R<2> r;
+    fast_two_sum(p, e, r.v[0], r.v[1]);
+    return r;
+}
+// quad-double: products of order 0..2 exact, order 3 rounded, order 4 dropped; each
+// order summed with two-sums whose errors fall into the next order.  ~107 FP64.
+__device__ __forceinline__ R<4> r_mul(R<4> a, R<4> b)
+{
+    double p00, e00, p01, e01, p10, e10, p02, e02, p11, e11, p20, e20;
+    two_prod(a.v[0], b.v[0], p00, e00);
+    two_prod(a.v[0], b.v[1], p01, e01);
+    two_prod(a.v[1], b.v[0], p10, e10);
+    two_prod(a.v[0], b.v[2], p02, e02);
+    two_prod(a.v[1], b.v[1], p11, e11);
+    two_prod(a.v[2], b.v[0], p20, e20);
+    double c1, u1, u2, s;
+    two_sum(p01, p10, s, u1);
+    two_sum(s, e00, c1, u2);                       // order 1
+    double c2, v1, v2, v3, v4, v5, v6;
+    two_sum(p02, p11, s, v1);
+    two_sum(s, p20, s, v2);
+    two_sum(s, e01, s, v3);
+    two_sum(s, e10, s, v4);
+    two_sum(s, u1, s, v5);
+    two_sum(s, u2, c2, v6);                        // order 2
+    double c3 = fma_(a.v[0], b.v[3], fma_(a.v[1], b.v[2], fma_(a.v[2], b.v[1], mul_(a.v[3], b.v[0]))));
+    c3 = add_(c3, add_(add_(e02, e11), e20));
+    c3 = add_(c3, add_(add_(add_(v1, v2), add_(v3, v4)), add_(v5, v6)));  // order 3
+    return renorm5(p00, c1, c2, c3, 0.0);
+}
+
+// times a double.  DD: 6 FP64.
+__device__ __forceinline__ R<1> r_mul_d(R<1> a, double d) { R<1> r; r.v[0] = mul_(a.v[0], d); return r; }
+__device__ __forceinline__ R<2> r_mul_d(R<2> a, double d)
+{
+    double p, e;
+    two_prod(a.v[0], d, p, e);
+    e = fma_(a.v[1], d, e);
+    R<2> r;
+    fast_two_sum(p, e, r.v[0], r.v[1]);
+    return r;
+}
+__device__ __forceinline__ R<4> r_mul_d(R<4> a, double d)
+{
+    double p0, e0, p1, e1, p2, e2;
+    two_prod(a.v[0], d, p0, e0);
+    two_prod(a.v[1], d, p1, e1);
+    two_prod(a.v[2], d, p2, e2);
+    double c1, u;
+    two_sum(p1, e0, c1, u);
+    double c2, w1, w2;
+    two_sum(p2, e1, c2, w1);
+    two_sum(c2, u, c2, w2);
+    double c3 = fma_(a.v[3], d, add_(add_(e2, w1), w2));
+    return renorm5(p0, c1, c2, c3, 0.0);
+}
+
+// ---------------------------------------------------------------- division
+// Long division: quotient digits q_j = r_lead / b_lead, remainder r -= q_j b exactly
+// to working precision, then the digits renormalised.
+__device__ __forceinline__ R<1> r_div(R<1> a, R<1> b) { R<1> r; r.v[0] = __ddiv_rn(a.v[0], b.v[0]); return r; }
+__device__ __forceinline__ R<2> r_div(R<2> a, R<2> b)
+{
+    double q1 = __ddiv_rn(a.v[0], b.v[0]);
+    R<2> r = r_sub(a, r_mul_d(b, q1));
+    double q2 = __ddiv_rn(r.v[0], b.v[0]);
+    r = r_sub(r, r_mul_d(b, q2));
+    double q3 = __ddiv_rn(r.v[0], b.v[0]);
+    double s, e;
+    fast_two_sum(q1, q2, s, e);
+    e = add_(e, q3);
+    R<2> out;
+    fast_two_sum(s, e, out.v[0], out.v[1]);
+    return out;
+}
+__device__ __forceinline__ R<4> r_div(R<4> a, R<4> b)
+{
+    double q[5];
+    R<4> r = a;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        q[j] = __ddiv_rn(r.v[0], b.v[0]);
+        if (j < 4) r = r_sub(r, r_mul_d(b, q[j]));
+    }
+    return renorm5(q[0], q[1], q[2], q[3], q[4]);
+}
+
+// ---------------------------------------------------------------- small integers
+// a * k for a small positive integer k; exact for powers of two.
+template <int L> __device__ __forceinline__ R<L> r_scale_int(R<L> a, int k)
+{
+    if (k == 1) return a;
+    if ((k & (k - 1)) == 0) {
+        double s = (double)k;
+#pragma unroll
+        for (int j = 0; j < L; j++) a.v[j] = mul_(a.v[j], s);
+        return a;
+    }
+    return r_mul_d(a, (double)k);
+}
+
+// ---------------------------------------------------------------- complex
+template <int L> __device__ __forceinline__ C<L> c_zero() { C<L> z; z.re = r_zero<L>(); z.im = r_zero<L>(); return z; }
+template <int L> __device__ __forceinline__ C<L> c_from(double re, double im)
+{
+    C<L> z;
+    z.re = r_from<L>(re);
+    z.im = r_from<L>(im);
+    return z;
+}
+template <int L> __device__ __forceinline__ C<L> c_add(C<L> a, C<L> b)
+{
+    C<L> z;
+    z.re = r_add(a.re, b.re);
+    z.im = r_add(a.im, b.im);
+    return z;
+}
+template <int L> __device__ __forceinline__ C<L> c_sub(C<L> a, C<L> b)
+{
+    C<L> z;
+    z.re = r_sub(a.re, b.re);
+    z.im = r_sub(a.im, b.im);
+    return z;
+}
+template <int L> __device__ __forceinline__ C<L> c_mul_d(C<L> a, double d)
+{
+    C<L> z;
+    z.re = r_mul_d(a.re, d);
+    z.im = r_mul_d(a.im, d);
+    return z;
+}
+template <int L> __device__ __forceinline__ C<L> c_mul_r(C<L> a, R<L> s)
+{
+    C<L> z;
+    z.re = r_mul(a.re, s);
+    z.im = r_mul(a.im, s);
+    return z;
+}
+template <int L> __device__ __forceinline__ C<L> c_scale_int(C<L> a, int k)
+{
+    C<L> z;
+    z.re = r_scale_int(a.re, k);
+    z.im = r_scale_int(a.im, k);
+    return z;
+}
+
+// generic complex product: four real products, two sums
+template <int L> __device__ __forceinline__ C<L> c_mul(C<L> a, C<L> b)
+{
+    C<L> z;
+    z.re = r_sub(r_mul(a.re, b.re), r_mul(a.im, b.im));
+    z.im = r_add(r_mul(a.re, b.im), r_mul(a.im, b.re));
+    return z;
+}
+// complex double: 4 FP64
+template <> __device__ __forceinline__ C<1> c_mul<1>(C<1> a, C<1> b)
+{
+    C<1> z;
+    z.re.v[0] = fma_(a.re.v[0], b.re.v[0], -mul_(a.im.v[0], b.im.v[0]));
+    z.im.v[0] = fma_(a.re.v[0], b.im.v[0], mul_(a.im.v[0], b.re.v[0]));
+    return z;
+}
+// complex double-double, each part as ONE fused dot product of two DD products:
+// exact leading products, their difference by two-sum, all order-1 terms (product
+// errors and the four cross terms) accumulated into the error by FMAs, one
+// renormalising fast-two-sum.  19 FP64 per part, 38 in all (50 for 4 mul + 2 add).
+__device__ __forceinline__ void dd_dot2(double a0, double a1, double b0, double b1,
+                                        double c0, double c1, double d0, double d1,
+                                        double &hi, double &lo)
+{
+    // a*b + c*d
+    double p, q, ep, eq, s, e;
+    two_prod(a0, b0, p, ep);
+    two_prod(c0, d0, q, eq);
+    two_sum(p, q, s, e);
+    e = add_(e, add_(ep, eq));
+    e = fma_(a0, b1, e);
+    e = fma_(a1, b0, e);
+    e = fma_(c0, d1, e);
+    e = fma_(c1, d0, e);
+    fast_two_sum(s, e, hi, lo);
+}
+template <> __device__ __forceinline__ C<2> c_mul<2>(C<2> a, C<2> b)
+{
+    C<2> z;
+    dd_dot2(a.re.v[0], a.re.v[1], b.re.v[0], b.re.v[1],
+            -a.im.v[0], -a.im.v[1], b.im.v[0], b.im.v[1], z.re.v[0], z.re.v[1]);
+    dd_dot2(a.re.v[0], a.re.v[1], b.im.v[0], b.im.v[1],
+            a.im.v[0], a.im.v[1], b.re.v[0], b.re.v[1], z.im.v[0], z.im.v[1]);
+    return z;
+}
+
+// 1 / b = conj(b) / |b|^2
+template <int L> __device__ __forceinline__ C<L> c_inv(C<L> b)
+{
+    R<L> den = r_add(r_mul(b.re, b.re), r_mul(b.im, b.im));
+    C<L> z;
+    z.re = r_div(b.re, den);
+    z.im = r_neg(r_div(b.im, den));
+    return z;
+}
+
+// |z|^2 of the leading limbs in plain double (pivot and norm measure): 3 FP64.
+template <int L> __device__ __forceinline__ double c_abs2_lead(const C<L> &z)
+{
+    return add_(mul_(z.re.v[0], z.re.v[0]), mul_(z.im.v[0], z.im.v[0]));
+}
+
+// z^e by binary powering, z^0 = 1
+template <int L> __device__ __forceinline__ C<L> c_pow(C<L> z, int e)
+{
+    C<L> r = c_from<L>(1.0, 0.0);
+    bool first = true;
+    while (e > 0) {
+        if (e & 1) {
+            r = first ? z : c_mul(r, z);
+            first = false;
+        }
+        e >>= 1;
+        if (e) z = c_mul(z, z);
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- structure-of-arrays I/O
+// A complex L-limb array stored as [2][L][...] with plane stride `plane` doubles:
+// part c (0 re, 1 im), limb l lives at base[(c * L + l) * plane + off].
+template <int L> __device__ __forceinline__ C<L> ld_c(const double *__restrict__ base, size_t plane, size_t off)
+{
+    C<L> z;
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        z.re.v[l] = base[(size_t)l * plane + off];
+        z.im.v[l] = base[(size_t)(L + l) * plane + off];
+    }
+    return z;
+}
+template <int L> __device__ __forceinline__ void st_c(double *__restrict__ base, size_t plane, size_t off, const C<L> &z)
+{
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+        base[(size_t)l * plane + off] = z.re.v[l];
+        base[(size_t)(L + l) * plane + off] = z.im.v[l];
+    }
+}
+// leading limbs only
+template <int L> __device__ __forceinline__ void ld_lead(const double *__restrict__ base, size_t plane, size_t off,
+                                                         double &re, double &im)
+{
+    re = base[off];
+    im = base[(size_t)L * plane + off];
+}
+
+template <int L> __device__ __forceinline__ bool c_finite_lead(const C<L> &z)
+{
+    return isfinite(z.re.v[0]) && isfinite(z.im.v[0]);
+}
+
+}  // namespace hc

@@ -1,0 +1,198 @@
+"""Thin ctypes binding of ``libhc.so`` (declared in ``include/hc.h``).
+
+The functions carry the C names and only marshal arguments: device buffers are torch
+CUDA tensors (or raw integer pointers), streams are torch streams.  Every step of the
+computation runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing, :func:`load` raises.
+
+Layout helpers convert complex numpy arrays to and from the library's
+structure-of-arrays layout ``[2][L][rows...][npts]`` (re limbs, im limbs; point index
+fastest).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HC_SUCCESS, HC_EINVAL, HC_ENOMEM, HC_ECUDA, HC_ENOTIMPL, HC_ETIMEOUT = 0, -1, -2, -3, -4, -5
+HC_OK, HC_NOCONV, HC_SINGULAR, HC_MIN_STEP, HC_MAX_STEPS, HC_DIVERGED, HC_NONFINITE = range(7)
+STATUS_NAMES = {0: "OK", 1: "NOCONV", 2: "SINGULAR", 3: "MIN_STEP", 4: "MAX_STEPS",
+                5: "DIVERGED", 6: "NONFINITE"}
+HC_LU_NATIVE, HC_LU_FP64_REFINE = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HCError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} failed with code {code}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Load libhc.so (building it first if allowed).  Raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libhc.so not built at {path}")
+            _build.build()
+        L = ct.CDLL(path)
+        vp, i, d = ct.c_void_p, ct.c_int, ct.c_double
+        i32p = ct.POINTER(ct.c_int32)
+        L.hc_system_load.argtypes = [ct.POINTER(vp), i, i, i32p, i32p, i32p, i32p,
+                                     ct.POINTER(ct.c_double), i, ct.POINTER(ct.c_double)]
+        L.hc_system_load.restype = i
+        L.hc_system_free.argtypes = [vp]
+        L.hc_system_free.restype = None
+        L.hc_system_info.argtypes = [vp] + [ct.POINTER(ct.c_int)] * 7
+        L.hc_system_info.restype = i
+        L.hc_eval_jac.argtypes = [vp, i, d, vp, vp, vp, vp]
+        L.hc_eval_jac.restype = i
+        L.hc_newton_step.argtypes = [vp, i, d, vp, i, i, vp, vp, vp, vp]
+        L.hc_newton_step.restype = i
+        L.hc_last_error.argtypes = []
+        L.hc_last_error.restype = ct.c_char_p
+        L.hc_probe_fp64_peak.argtypes = [ct.POINTER(ct.c_double)]
+        L.hc_probe_fp64_peak.restype = i
+        L.hc_set_tiles.argtypes = [i, i]
+        L.hc_set_tiles.restype = i
+        _lib = L
+        return L
+
+
+def hc_last_error() -> str:
+    return load().hc_last_error().decode()
+
+
+def _check(fn: str, rc: int) -> int:
+    if rc != HC_SUCCESS:
+        raise HCError(fn, rc, hc_last_error())
+    return rc
+
+
+def _ptr(a) -> int | None:
+    """Device pointer of a torch tensor (or an int pointer / None)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    return a.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ct.POINTER(ct.c_int32))
+
+
+class System:
+    """An uploaded system (hc_system_load); frees itself (hc_system_free)."""
+
+    def __init__(self, handle, n, npoly, prec):
+        self.handle = handle
+        self.n, self.npoly, self.prec = n, npoly, prec
+
+    def info(self) -> dict:
+        vals = [ct.c_int() for _ in range(7)]
+        _check("hc_system_info", load().hc_system_info(self.handle, *[ct.byref(v) for v in vals]))
+        keys = ("n", "npoly", "nmon", "nvar", "prec", "max_exp", "max_deg")
+        return {k: v.value for k, v in zip(keys, vals)}
+
+    def free(self):
+        if self.handle:
+            load().hc_system_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hc_system_load(n, npoly, mon_ptr, var_ptr, var_idx, var_exp, coef, prec, gamma) -> System:
+    """coef: float64 [nmon][2][L]; gamma: (re, im)."""
+    L = load()
+    mp, mpp = _i32(mon_ptr)
+    vp, vpp = _i32(var_ptr)
+    vi, vip = _i32(var_idx if len(var_idx) else np.zeros(1, np.int32))
+    ve, vep = _i32(var_exp if len(var_exp) else np.ones(1, np.int32))
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(2))
+    h = ct.c_void_p()
+    _check("hc_system_load", L.hc_system_load(
+        ct.byref(h), int(n), int(npoly), mpp, vpp, vip, vep,
+        c.ctypes.data_as(ct.POINTER(ct.c_double)), int(prec),
+        g.ctypes.data_as(ct.POINTER(ct.c_double))))
+    return System(h.value, int(n), int(npoly), int(prec))
+
+
+def system_from(s, prec: int, gamma: complex) -> System:
+    """Load a :class:`paper_1109_0545_gb300.synth.System`."""
+    return hc_system_load(s.n, s.npoly, s.mon_ptr, s.var_ptr, s.var_idx, s.var_exp,
+                          s.coef_limbs(prec), prec, (gamma.real, gamma.imag))
+
+
+def hc_eval_jac(sys: System, npts: int, t: float, x, f, J=None, stream=None) -> None:
+    _check("hc_eval_jac", load().hc_eval_jac(sys.handle, int(npts), float(t), _ptr(x), _ptr(f),
+                                             _ptr(J), _stream(stream)))
+
+
+def hc_newton_step(sys: System, npts: int, t: float, x, lu_mode: int, max_refine: int,
+                   res_norm, status, sweeps=None, stream=None) -> None:
+    _check("hc_newton_step", load().hc_newton_step(
+        sys.handle, int(npts), float(t), _ptr(x), int(lu_mode), int(max_refine), _ptr(res_norm),
+        _ptr(status), _ptr(sweeps), _stream(stream)))
+
+
+def hc_probe_fp64_peak() -> float:
+    v = ct.c_double()
+    _check("hc_probe_fp64_peak", load().hc_probe_fp64_peak(ct.byref(v)))
+    return v.value
+
+
+def hc_set_tiles(rows_per_task: int, blocks_per_sm: int) -> None:
+    _check("hc_set_tiles", load().hc_set_tiles(int(rows_per_task), int(blocks_per_sm)))
+
+
+# ----------------------------------------------------------------------------- layouts
+def to_soa(z: np.ndarray, L: int, limbs: np.ndarray | None = None) -> np.ndarray:
+    """complex [npts][rows...] (leading limbs) or limbs [npts][rows...][2][L] ->
+    float64 [2][L][rows...][npts]."""
+    if limbs is None:
+        z = np.asarray(z, dtype=np.complex128)
+        limbs = np.zeros(z.shape + (2, L))
+        limbs[..., 0, 0] = z.real
+        limbs[..., 1, 0] = z.imag
+    nd = limbs.ndim
+    # [npts, rows..., 2, L] -> [2, L, rows..., npts]
+    perm = (nd - 2, nd - 1) + tuple(range(1, nd - 2)) + (0,)
+    return np.ascontiguousarray(np.transpose(limbs, perm))
+
+
+def from_soa(a: np.ndarray) -> np.ndarray:
+    """float64 [2][L][rows...][npts] -> limbs [npts][rows...][2][L]."""
+    nd = a.ndim
+    perm = (nd - 1,) + tuple(range(2, nd - 1)) + (0, 1)
+    return np.ascontiguousarray(np.transpose(a, perm))

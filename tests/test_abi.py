@@ -1,0 +1,115 @@
+"""The C ABI on the host: the library loads, exports every symbol the header declares,
+and rejects malformed input with HC_EINVAL before touching the device."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1109_0545_gb300 import hc, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(hc_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for want in ("hc_system_load", "hc_system_free", "hc_eval_jac", "hc_newton_step",
+                 "hc_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hc.load()
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def _load(s, prec=2, **over):
+    d = dict(n=s.n, npoly=s.npoly, mon_ptr=s.mon_ptr.copy(), var_ptr=s.var_ptr.copy(),
+             var_idx=s.var_idx.copy(), var_exp=s.var_exp.copy(),
+             coef=s.coef_limbs(prec if prec in (1, 2, 4) else 2),
+             prec=prec, gamma=(0.6, 0.8))
+    d.update(over)
+    return hc.hc_system_load(d["n"], d["npoly"], d["mon_ptr"], d["var_ptr"], d["var_idx"],
+                             d["var_exp"], d["coef"], d["prec"], d["gamma"])
+
+
+@pytest.fixture
+def small():
+    return synth.random_system(np.random.default_rng(5), 4, 3, 2, (1, 3), const_term=True)
+
+
+def test_rejects_unsorted_indices(small):
+    vi = small.var_idx.copy()
+    vi[0], vi[1] = vi[1], vi[0]
+    with pytest.raises(hc.HCError) as e:
+        _load(small, var_idx=vi)
+    assert e.value.code == hc.HC_EINVAL and "increasing" in str(e.value)
+
+
+def test_rejects_zero_exponent(small):
+    ve = small.var_exp.copy()
+    ve[2] = 0
+    with pytest.raises(hc.HCError) as e:
+        _load(small, var_exp=ve)
+    assert e.value.code == hc.HC_EINVAL
+
+
+def test_rejects_index_out_of_range(small):
+    vi = small.var_idx.copy()
+    vi[-1] = small.n
+    with pytest.raises(hc.HCError) as e:
+        _load(small, var_idx=vi)
+    assert e.value.code == hc.HC_EINVAL
+
+
+def test_rejects_nonfinite_coefficient(small):
+    c = small.coef_limbs(2)
+    c[1, 0, 1] = np.nan
+    with pytest.raises(hc.HCError) as e:
+        _load(small, coef=c)
+    assert e.value.code == hc.HC_EINVAL and "finite" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [0, 3, 8])
+def test_rejects_bad_precision(small, prec):
+    with pytest.raises(hc.HCError) as e:
+        _load(small, prec=prec, coef=small.coef_limbs(2))
+    assert e.value.code == hc.HC_EINVAL
+
+
+def test_rejects_too_many_variables_per_monomial():
+    n = 70
+    s = synth.System(n=n, npoly=1, mon_ptr=np.array([0, 1], np.int32),
+                     var_ptr=np.array([0, 33], np.int32), var_idx=np.arange(33, dtype=np.int32),
+                     var_exp=np.ones(33, np.int32), coef=np.array([1.0 + 0j]))
+    with pytest.raises(hc.HCError) as e:
+        _load(s)
+    assert e.value.code == hc.HC_EINVAL
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = hc.load()
+    assert lib.hc_eval_jac(None, 1, 0.5, None, None, None, None) == hc.HC_EINVAL
+    assert lib.hc_newton_step(None, 1, 0.5, None, 0, 1, None, None, None, None) == hc.HC_EINVAL
+    lib.hc_system_free(None)  # no-op
+
+
+def test_layout_round_trip():
+    rng = np.random.default_rng(3)
+    limbs = rng.normal(size=(7, 5, 3, 2, 2))
+    soa = hc.to_soa(None, 2, limbs)
+    assert soa.shape == (2, 2, 5, 3, 7)
+    assert soa[1, 0, 4, 2, 6] == limbs[6, 4, 2, 1, 0]
+    assert np.array_equal(hc.from_soa(soa), limbs)
