@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: one Newton step (Alg. 4.1 loop body: evaluation of the
+homotopy and its full Jacobian by the scheme of Sec. 6, residual, FP64 LU + DD
+refinement of the Newton system, update) at every point of the eval-throughput
+workload -- n = 32 unknowns, 32 polynomials x 128 monomials, 6 variables per monomial,
+exponents 1..4, unit-circle coefficients, 65,536 points on the unit torus, complex
+double-double -- through the C-ABI library.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank runs its own 65,536 points
+(independent problems, weak scaling, no collective on the data path); the timing is
+barrier-bracketed and the max over ranks.  ``--impl reference`` times the CPU oracle
+on the host cores instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DD eval+Jacobian points/s, path steps/s vs plain GPU at 1e-28; FP64 roof %"
+WORKLOAD = ("Newton step (eval+Jacobian+homotopy, FP64 LU + DD refinement, update) per point; "
+            "n=32, 32x128 monomials, k=6, exponents 1..4, unit-circle coefficients, "
+            "65,536 unit-torus points, complex double-double, seed 2")
+T_HOM = 0.5
+MAX_REFINE = 6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--npts", type=int, default=65536)
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str | None):
+        self.proc = None
+        self.path = None
+        self.dev_id = dev_id
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.dev_id:
+                cmd += ["-i", self.dev_id]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ CPU arm
+def oracle_points_per_s(s, pts, gamma, budget_s: float, lu_mode: int = 1):
+    """Time the oracle's threaded Newton step on a bounded sample of the points."""
+    import numpy as np
+
+    import oracle
+    from paper_1109_0545_gb300 import synth
+    cores = os.cpu_count() or 1
+    g = np.array([gamma.real, gamma.imag])
+    # calibrate on one point per core
+    probe = synth.limbs(pts[:cores], 2)
+    t0 = time.perf_counter()
+    oracle.newton_threads(s.as_dict(), s.coef_limbs(2), probe, T_HOM, g, lu_mode, MAX_REFINE, cores)
+    per_wave = max(time.perf_counter() - t0, 1e-3)
+    waves = max(1, int(budget_s / per_wave))
+    n = min(len(pts), waves * cores)
+    sample = synth.limbs(pts[:n], 2)
+    t0 = time.perf_counter()
+    oracle.newton_threads(s.as_dict(), s.coef_limbs(2), sample, T_HOM, g, lu_mode, MAX_REFINE, cores)
+    dt = time.perf_counter() - t0
+    return n / dt, cores, n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1109_0545_gb300 import synth
+    s, pts, gamma = synth.eval_throughput(2, npts=args.npts)
+    steps = []
+    cores = os.cpu_count() or 1
+    budget = 2.0
+    for k in range(args.warmup + args.steps):
+        v, cores, n, dt = oracle_points_per_s(s, pts, gamma, budget)
+        if k >= args.warmup:
+            steps.append((n, dt))
+    tot_n = sum(n for n, _ in steps)
+    tot_t = sum(t for _, t in steps)
+    value = tot_n / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / max(len(steps), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "npts": args.npts, "n": 32, "precision": "complex DD",
+                   "lu": "FP64 LU + DD refinement"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{steps[0][0] if steps else 0} points per step "
+                                   f"(about {budget:.0f} s of oracle work), all host cores"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def captured_traffic(npts: int):
+    """DRAM bytes of one evaluation launch from the committed ncu summary, scaled by
+    points -- or None once the kernel sources differ from the captured ones."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "eval_jac_dd_8192pts_ncu.md")
+    srcs = ["points.cuh", "mp.cuh", "hc_eval.cu"]
+    try:
+        text = open(path).read()
+        h = hashlib.sha256()
+        for name in srcs:
+            with open(os.path.join(ROOT, "paper_1109_0545_gb300", "csrc", name), "rb") as fh:
+                h.update(fh.read())
+        sha = re.search(r"counters_source_sha256:\s*([0-9a-f]+)", text).group(1)
+        per_pt = float(re.search(r"dram_bytes_per_point:\s*([0-9.]+)", text).group(1))
+    except (OSError, AttributeError):
+        return None
+    if not h.hexdigest().startswith(sha):
+        return None
+    return per_pt * npts
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1109_0545_gb300 import hc, opcount, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    hc.load(build_if_missing=False)
+
+    L = 2
+    npts = args.npts
+    s, pts, gamma = synth.eval_throughput(2, npts=npts)
+    if rank > 0:
+        pts = synth.torus_points(np.random.default_rng([2, rank]), npts, s.n)
+    sysh = hc.system_from(s, L, gamma)
+    stream = torch.cuda.current_stream()
+    x0 = torch.from_numpy(hc.to_soa(pts, L)).cuda()
+    x = x0.clone()
+    res = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    st = torch.zeros(npts, dtype=torch.int32, device="cuda")
+    sw = torch.zeros(npts, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def step(lu=hc.HC_LU_FP64_REFINE):
+        hc.hc_newton_step(sysh, npts, T_HOM, x, lu, MAX_REFINE, res, st, sw, stream)
+
+    for _ in range(max(args.warmup, 0)):
+        x.copy_(x0)
+        step()
+    torch.cuda.synchronize()
+    peak_gops = hc.hc_probe_fp64_peak()
+
+    dev_id = None
+    try:
+        dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        dev_id = None
+    clocks = ClockSampler(dev_id)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    hc.hc_prof_read()          # drop anything recorded earlier
+    hc.hc_prof_enable(True)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        x.copy_(x0)            # restore the input point set (outside the step's events)
+        flush.zero_()          # evict L2 between timed steps
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    hc.hc_prof_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    eval_ms, eval_launches = hc.hc_prof_read()
+    if dist:
+        tmax = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        total_ms = float(tmax.item())
+    value = npts * world * args.steps / (total_ms * 1e-3)
+    status = st.cpu().numpy()
+    sweeps = sw.cpu().numpy()
+
+    ops_pt = opcount.eval_ops_per_point(s, L)
+    eval_avg_ms = eval_ms / max(eval_launches, 1)
+    achieved = ops_pt * npts / (eval_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak_gops,
+                "unit": "G FP64 instr/s", "frac": achieved / peak_gops,
+                "peak_source": "measured live (hc_probe_fp64_peak, independent DFMA chains)",
+                "kernel": "k_eval_pts<DD,jacobian>", "ops_per_point": ops_pt,
+                "kernel_ms": eval_avg_ms, "traffic": captured_traffic(npts),
+                "traffic_note": "ncu dram read+write per launch, 8,192-point capture scaled by points"}
+
+    extras = {}
+    if not args.no_extras:
+        # the plain all-DD elimination, and evaluation alone, same points
+        def timed(fn, reps=3):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            best = 1e30
+            for _ in range(reps):
+                x.copy_(x0)
+                flush.zero_()
+                ev0.record(stream)
+                fn()
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, ev0.elapsed_time(ev1))
+            return best
+        ms_native = timed(lambda: step(hc.HC_LU_NATIVE))
+        f = torch.empty((2, L, s.npoly, npts), dtype=torch.float64, device="cuda")
+        J = torch.empty((2, L, s.npoly, s.n, npts), dtype=torch.float64, device="cuda")
+        ms_eval = timed(lambda: hc.hc_eval_jac(sysh, npts, T_HOM, x, f, J, stream))
+        del f, J
+        extras = {"newton_native_dd_lu_points_per_s": npts / (ms_native * 1e-3),
+                  "eval_jac_points_per_s": npts / (ms_eval * 1e-3),
+                  "refine_sweeps_hist": np.bincount(sweeps, minlength=MAX_REFINE + 1).tolist(),
+                  "status_ok_frac": float(np.mean(status == hc.HC_OK))}
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    x_host = torch.from_numpy(hc.to_soa(pts, L)).pin_memory()
+    x_out = torch.empty_like(x_host).pin_memory()
+    st_host = torch.empty(npts, dtype=torch.int32).pin_memory()
+    res_host = torch.empty(npts, dtype=torch.float64).pin_memory()
+    e2e_steps = min(args.steps, 5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(x_host, non_blocking=True)
+        step()
+        x_out.copy_(x, non_blocking=True)
+        st_host.copy_(st, non_blocking=True)
+        res_host.copy_(res, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = x_host.numel() * 8
+    d2h = x_out.numel() * 8 + npts * 4 + npts * 8
+    e2e = {"value": npts * e2e_steps / e2e_s, "unit": "points/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        v, cores, n, dt = oracle_points_per_s(s, pts, gamma, budget_s=15.0)
+        cpu = {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} of {npts} points, one Newton step each (FP64 LU + DD "
+                         f"refinement), {dt:.1f} s on {cores} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "npts": npts, "n": s.n, "monomials": s.nmon,
+                       "precision": "complex double-double", "lu": "FP64 LU + DD refinement",
+                       "max_refine": MAX_REFINE, "t": T_HOM, "parallelism": f"dp{world}",
+                       "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": clk, "wall_s": t_wall,
+            "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    sysh.free()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,16 @@ const char *hc_last_error(void);
  */
 int hc_probe_fp64_peak(double *gops);
 
+/*
+ * hc_prof_enable / hc_prof_read -- measurement helpers, not part of the method.  While
+ * enabled, every launch of the evaluation kernel is bracketed by two CUDA events on the
+ * stream it runs on.  hc_prof_read waits for the recorded launches, returns their summed
+ * device time in milliseconds and their number, and forgets them.  Host-side state,
+ * process-wide; not thread-safe.  Errors: HC_ECUDA.
+ */
+int hc_prof_enable(int on);
+int hc_prof_read(double *ms, int *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1190,3 +1190,55 @@ int or_eval_threads(int L, int n, int npoly, const int32_t *mon_ptr, const int32
     free(jobs);
     return rc;
 }
+
+/* Threaded batch driver for the CPU baseline: or_newton_step over points on nthreads
+ * POSIX threads, each thread a contiguous block of points. */
+typedef struct {
+    int L, n;
+    const int32_t *mon_ptr, *var_ptr, *var_idx, *var_exp;
+    const double *coef, *gamma;
+    double t, *x, *res;
+    int32_t *status, *sweeps;
+    int lu_mode, max_refine, p0, p1, rc;
+} newton_job;
+
+static void *newton_worker(void *arg)
+{
+    newton_job *j = (newton_job *)arg;
+    size_t w = (size_t)j->n * 2 * j->L;
+    j->rc = or_newton_step(j->L, j->n, j->mon_ptr, j->var_ptr, j->var_idx, j->var_exp, j->coef,
+                           j->p1 - j->p0, j->t, j->gamma, j->x + (size_t)j->p0 * w, j->lu_mode,
+                           j->max_refine, j->res + j->p0, j->status + j->p0, j->sweeps + j->p0);
+    return NULL;
+}
+
+int or_newton_threads(int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr,
+                      const int32_t *var_idx, const int32_t *var_exp, const double *coef,
+                      int npts, double t, const double *gamma, double *x, int lu_mode,
+                      int max_refine, double *res_norm, int32_t *status, int32_t *sweeps,
+                      int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > npts) nthreads = npts > 0 ? npts : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    newton_job *jobs = (newton_job *)malloc(sizeof(newton_job) * (size_t)nthreads);
+    for (int k = 0; k < nthreads; k++) {
+        newton_job *j = &jobs[k];
+        j->L = L; j->n = n;
+        j->mon_ptr = mon_ptr; j->var_ptr = var_ptr; j->var_idx = var_idx; j->var_exp = var_exp;
+        j->coef = coef; j->gamma = gamma; j->t = t; j->x = x; j->res = res_norm;
+        j->status = status; j->sweeps = sweeps; j->lu_mode = lu_mode; j->max_refine = max_refine;
+        j->p0 = (int)((long)npts * k / nthreads);
+        j->p1 = (int)((long)npts * (k + 1) / nthreads);
+        j->rc = 0;
+        pthread_create(&th[k], NULL, newton_worker, j);
+    }
+    int rc = 0;
+    for (int k = 0; k < nthreads; k++) {
+        pthread_join(th[k], NULL);
+        if (jobs[k].rc) rc = jobs[k].rc;
+    }
+    free(th);
+    free(jobs);
+    return rc;
+}

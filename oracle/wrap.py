@@ -92,6 +92,11 @@ def lib():
                                          np.ctypeslib.ndpointer(dtype=np.int32),
                                          np.ctypeslib.ndpointer(dtype=np.int32)]
             L.or_newton_step.restype = i
+            L.or_newton_threads.argtypes = [i, i, _I32P, _I32P, _I32P, _I32P, _F64P, i, d, _F64P,
+                                            _F64P, i, i, _F64P,
+                                            np.ctypeslib.ndpointer(dtype=np.int32),
+                                            np.ctypeslib.ndpointer(dtype=np.int32), i]
+            L.or_newton_threads.restype = i
             L.or_track.argtypes = [i, i, _I32P, _I32P, _I32P, _I32P, _F64P, _F64P, _F64P,
                                    ct.POINTER(TrackOpts), _F64P, ct.POINTER(_Stats), p,
                                    ct.POINTER(ct.c_int32)]
@@ -212,6 +217,22 @@ def newton_step(sysd, coef, x, t, gamma, lu_mode=0, max_refine=4):
                               _f64(gamma), x, lu_mode, max_refine, res, st, sw)
     if rc != 0:
         raise ValueError(f"or_newton_step failed ({rc})")
+    return x, res, st, sw
+
+
+def newton_threads(sysd, coef, x, t, gamma, lu_mode=0, max_refine=4, nthreads=None):
+    """newton_step split over POSIX threads (CPU baseline)."""
+    L = coef.shape[-1]
+    x = _f64(x).copy()
+    npts = x.shape[0]
+    res = np.zeros(npts)
+    st = np.zeros(npts, dtype=np.int32)
+    sw = np.zeros(npts, dtype=np.int32)
+    nthreads = nthreads or os.cpu_count() or 1
+    rc = lib().or_newton_threads(L, sysd["n"], *_sysargs(sysd), _f64(coef), npts, float(t),
+                                 _f64(gamma), x, lu_mode, max_refine, res, st, sw, nthreads)
+    if rc != 0:
+        raise ValueError(f"or_newton_threads failed ({rc})")
     return x, res, st, sw
 
 

@@ -86,10 +86,12 @@ int launch_eval(const DevSys &S, int npts, double t, const double *X, double *PW
     const long long need = (tasks + wpb - 1) / wpb;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
+    hc_prof_mark(st, true);
     if (J)
         k_eval_pts<L, true><<<(int)grid, 32 * wpb, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
     else
         k_eval_pts<L, false><<<(int)grid, 32 * wpb, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
+    hc_prof_mark(st, false);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return hc_cuda_fail(e, "k_eval_pts launch");
     return HC_SUCCESS;

@@ -48,6 +48,10 @@ int hc_cuda_fail(cudaError_t e, const char *what);
 // workspace of at least `bytes`, 256-byte aligned; grows (synchronising) if needed
 int hc_workspace(hc_system *s, size_t bytes, void **out);
 
+// event timing of the evaluation kernel (hc_prof_enable / hc_prof_read)
+bool hc_prof_on(void);
+void hc_prof_mark(cudaStream_t st, bool begin);
+
 // number of SMs of the current device (cached)
 int hc_num_sms(void);
 

@@ -41,6 +41,53 @@ int hc_num_sms(void)
     return cached[dev];
 }
 
+// ---------------------------------------------------------------------------------
+// Event timing of the evaluation kernel: each launch is bracketed by two events on the
+// stream it runs on; hc_prof_read waits for them and sums the intervals.
+// ---------------------------------------------------------------------------------
+#include <vector>
+static bool g_prof = false;
+static std::vector<cudaEvent_t> g_prof_ev;  // begin, end, begin, end, ...
+
+bool hc_prof_on(void) { return g_prof; }
+
+void hc_prof_mark(cudaStream_t st, bool begin)
+{
+    if (!g_prof) return;
+    if (begin != (g_prof_ev.size() % 2 == 0)) return;  // keep begin/end paired
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, st);
+    g_prof_ev.push_back(e);
+}
+
+extern "C" int hc_prof_enable(int on)
+{
+    g_prof = on != 0;
+    return HC_SUCCESS;
+}
+
+extern "C" int hc_prof_read(double *ms, int *launches)
+{
+    double total = 0.0;
+    int n = 0;
+    cudaError_t err = cudaSuccess;
+    for (size_t i = 0; i + 1 < g_prof_ev.size(); i += 2) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(g_prof_ev[i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, g_prof_ev[i], g_prof_ev[i + 1]);
+        if (e != cudaSuccess) err = e;
+        total += t;
+        n++;
+    }
+    for (cudaEvent_t e : g_prof_ev) cudaEventDestroy(e);
+    g_prof_ev.clear();
+    if (ms) *ms = total;
+    if (launches) *launches = n;
+    if (err != cudaSuccess) return hc_cuda_fail(err, "hc_prof_read");
+    return HC_SUCCESS;
+}
+
 int hc_workspace(hc_system *s, size_t bytes, void **out)
 {
     if (bytes == 0) bytes = 256;

@@ -70,6 +70,10 @@ def load(build_if_missing: bool = True):
         L.hc_probe_fp64_peak.restype = i
         L.hc_set_tiles.argtypes = [i, i]
         L.hc_set_tiles.restype = i
+        L.hc_prof_enable.argtypes = [i]
+        L.hc_prof_enable.restype = i
+        L.hc_prof_read.argtypes = [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]
+        L.hc_prof_read.restype = i
         _lib = L
         return L
 
@@ -174,6 +178,16 @@ def hc_probe_fp64_peak() -> float:
 
 def hc_set_tiles(rows_per_task: int, blocks_per_sm: int) -> None:
     _check("hc_set_tiles", load().hc_set_tiles(int(rows_per_task), int(blocks_per_sm)))
+
+
+def hc_prof_enable(on: bool) -> None:
+    _check("hc_prof_enable", load().hc_prof_enable(1 if on else 0))
+
+
+def hc_prof_read() -> tuple[float, int]:
+    ms, n = ct.c_double(), ct.c_int()
+    _check("hc_prof_read", load().hc_prof_read(ct.byref(ms), ct.byref(n)))
+    return ms.value, n.value
 
 
 # ----------------------------------------------------------------------------- layouts

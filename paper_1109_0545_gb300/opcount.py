@@ -1,0 +1,71 @@
+"""Static count of the FP64 instructions the evaluation kernel issues per point.
+
+The roofline of the evaluation kernel is the FP64 pipe, so its algorithmic work is the
+number of FP64 instructions (DADD, DMUL, DFMA, each one instruction) that the kernel's
+arithmetic executes for one point.  The per-operation counts below are those of
+``csrc/mp.cuh`` (stated there beside each routine); the per-monomial and per-row
+structure is that of ``csrc/points.cuh``.  ncu's per-thread FP64 instruction counters
+(``smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum``) check the total.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# FP64 instructions per operation, per limb count L
+C_MUL = {1: 4, 2: 38, 4: 4 * 107 + 2 * 80}
+C_ADD = {1: 2, 2: 22, 4: 2 * 80}
+R_ADD = {1: 1, 2: 11, 4: 80}
+C_MUL_D = {1: 2, 2: 12, 4: 2 * 61}
+
+
+def scale_int(L: int, k: int) -> int:
+    """c_scale_int: free for 1, 2L DMULs per part for powers of two, else c_mul_d."""
+    if k == 1:
+        return 0
+    if k & (k - 1) == 0:
+        return 2 * L
+    return C_MUL_D[L]
+
+
+def pow_mults(e: int) -> int:
+    """Multiplications of c_pow (binary powering) for exponent e."""
+    if e <= 0:
+        return 0
+    return (bin(e).count("1") - 1) + (e.bit_length() - 1)
+
+
+def eval_ops_per_point(s, L: int, homotopy: bool = True, jac: bool = True) -> int:
+    """FP64 instructions of the evaluation kernel for one point of system ``s``."""
+    cm, ca = C_MUL[L], C_ADD[L]
+    total = 0
+    vp, ve = s.var_ptr, s.var_exp
+    for m in range(s.nmon):
+        k = int(vp[m + 1] - vp[m])
+        ex = ve[vp[m]:vp[m + 1]]
+        if k == 0:
+            total += ca
+            continue
+        n2 = int(np.sum(ex >= 2))
+        if not jac:
+            total += (n2 + k) * cm + ca
+            continue
+        nmul = n2 + (3 * k - 3 if k >= 2 else 1)
+        total += nmul * cm + (k + 1) * ca + sum(scale_int(L, int(a)) for a in ex)
+    if homotopy:
+        deg = np.zeros(s.npoly, dtype=np.int64)
+        for i in range(s.npoly):
+            for m in range(s.mon_ptr[i], s.mon_ptr[i + 1]):
+                deg[i] = max(deg[i], int(ve[vp[m]:vp[m + 1]].sum()))
+        for i in range(s.npoly):
+            d = int(deg[i])
+            row = (pow_mults(d - 1) + 2) * cm + R_ADD[L] + C_MUL_D[L] + ca
+            if jac:
+                row += s.n * C_MUL_D[L] + scale_int(L, d) + cm + ca
+            total += row
+    return total
+
+
+def powers_ops_per_point(s, L: int) -> int:
+    """FP64 instructions of the power-table kernel for one point."""
+    emax = int(s.var_exp.max()) if len(s.var_exp) else 1
+    return s.n * max(emax - 2, 0) * C_MUL[L]
