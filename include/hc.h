@@ -146,6 +146,34 @@ const char *hc_last_error(void);
 int hc_probe_fp64_peak(double *gops);
 
 /*
+ * hc_eval_jac_noalloc -- hc_eval_jac for callers that cannot allocate device memory.
+ * The paper has no counterpart: this entry point exists for users of the library.
+ *
+ * hc_eval_jac allocates its workspace on first use.  A caller whose device memory is
+ * owned by its own pool allocator (a framework's caching allocator, a server that
+ * reserves a fixed budget at start-up) cannot allow that: the library's cudaMalloc could
+ * fail or fragment the pool, and cudaMalloc/cudaFree may synchronise the device inside a
+ * latency-critical loop.  This variant calls no allocating routine.  Its workspace is a
+ * fixed 32 MiB (33,554,432-byte) array compiled into the library as a device global; a
+ * device holds it from the first call on that device (from module load where lazy
+ * loading is off) until the process exits.
+ *   - A call needing more workspace than that fails with HC_EINVAL before any launch.
+ *     The workspace is the power table, (max_exp - 2) * 2 * L * n * npts doubles
+ *     (none when every exponent is at most 2): e.g. at most 16,384 points per call for
+ *     n = 32, exponents up to 4, DD.  Split larger point sets over several calls.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - Every call uses the same array: calls whose kernels overlap on the GPU (other
+ *     streams, other host threads) race on it, so serialise them.  Each call writes the
+ *     whole table before reading it, so the previous call's contents do no harm.
+ *   - The event-timing helper below must be off (its default): it creates CUDA events.
+ * Arguments, layouts, results and other errors are those of hc_eval_jac.
+ */
+int hc_eval_jac_noalloc(hc_system *sys, int npts, double t, const double *x, double *f,
+                        double *J, void *stream);
+
+/*
  * hc_prof_enable / hc_prof_read -- measurement helpers, not part of the method.  While
  * enabled, every launch of the evaluation kernel is bracketed by two CUDA events on the
  * stream it runs on.  hc_prof_read waits for the recorded launches, returns their summed

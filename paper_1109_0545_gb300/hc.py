@@ -70,6 +70,8 @@ def load(build_if_missing: bool = True):
         L.hc_probe_fp64_peak.restype = i
         L.hc_set_tiles.argtypes = [i, i]
         L.hc_set_tiles.restype = i
+        L.hc_eval_jac_noalloc.argtypes = [vp, i, d, vp, vp, vp, vp]
+        L.hc_eval_jac_noalloc.restype = i
         L.hc_prof_enable.argtypes = [i]
         L.hc_prof_enable.restype = i
         L.hc_prof_read.argtypes = [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]
@@ -161,6 +163,12 @@ def system_from(s, prec: int, gamma: complex) -> System:
 def hc_eval_jac(sys: System, npts: int, t: float, x, f, J=None, stream=None) -> None:
     _check("hc_eval_jac", load().hc_eval_jac(sys.handle, int(npts), float(t), _ptr(x), _ptr(f),
                                              _ptr(J), _stream(stream)))
+
+
+def hc_eval_jac_noalloc(sys: System, npts: int, t: float, x, f, J=None, stream=None) -> None:
+    """hc_eval_jac with the library's fixed 32 MiB device workspace: allocates nothing."""
+    _check("hc_eval_jac_noalloc", load().hc_eval_jac_noalloc(
+        sys.handle, int(npts), float(t), _ptr(x), _ptr(f), _ptr(J), _stream(stream)))
 
 
 def hc_newton_step(sys: System, npts: int, t: float, x, lu_mode: int, max_refine: int,
