@@ -106,13 +106,13 @@ __global__ void __launch_bounds__(64) k_newton_native(int n, int npts, double *_
         for (int i = k + 1; i < n; i++) {
             const C<L> l = c_mul(ld_c<L>(A, aplane, AO(i, k)), inv);
             for (int j = k + 1; j < n; j++)
-                st_c<L>(A, aplane, AO(i, j), c_sub(ld_c<L>(A, aplane, AO(i, j)), c_mul(l, ld_c<L>(A, aplane, AO(k, j)))));
-            st_c<L>(H, hplane, HO(i), c_sub(ld_c<L>(H, hplane, HO(i)), c_mul(l, hk)));
+                st_c<L>(A, aplane, AO(i, j), c_fnma(ld_c<L>(A, aplane, AO(i, j)), l, ld_c<L>(A, aplane, AO(k, j))));
+            st_c<L>(H, hplane, HO(i), c_fnma(ld_c<L>(H, hplane, HO(i)), l, hk));
         }
     }
     for (int i = n - 1; i >= 0; i--) {
         C<L> s = ld_c<L>(H, hplane, HO(i));
-        for (int j = i + 1; j < n; j++) s = c_sub(s, c_mul(ld_c<L>(A, aplane, AO(i, j)), ld_c<L>(H, hplane, HO(j))));
+        for (int j = i + 1; j < n; j++) s = c_fnma(s, ld_c<L>(A, aplane, AO(i, j)), ld_c<L>(H, hplane, HO(j)));
         st_c<L>(H, hplane, HO(i), c_mul(s, ld_c<L>(A, aplane, AO(i, i))));
     }
     status[p] = apply_update<L>(n, npts, p, X, H, true);
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(64) k_newton_mixed(int n, int npts, double *__
             C<L> acc = ld_c<L>(H, hplane, HO(i));
             acc.re = r_neg(acc.re);
             acc.im = r_neg(acc.im);
-            for (int j = 0; j < n; j++) acc = c_sub(acc, c_mul(ld_c<L>(A, aplane, AO(i, j)), ld_c<L>(DZ, hplane, HO(j))));
+            for (int j = 0; j < n; j++) acc = c_fnma(acc, ld_c<L>(A, aplane, AO(i, j)), ld_c<L>(DZ, hplane, HO(j)));
             RV[HO(i)] = acc.re.v[0];
             RV[hplane + HO(i)] = acc.im.v[0];
         }

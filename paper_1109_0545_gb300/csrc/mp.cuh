@@ -39,6 +39,28 @@ __device__ __forceinline__ void fast_two_sum(double a, double b, double &s, doub
     e = sub_(b, sub_(s, a));
 }
 
+// s + e = a + b exactly for any a, b: order the operands by magnitude, comparing the
+// bit patterns as integers (the INT pipe; GB300's FP64 pipe is ~40x scarcer), then
+// Dekker's fast two-sum.  3 FP64.
+__device__ __forceinline__ void two_sum_ord(double a, double b, double &s, double &e)
+{
+    const unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
+    const unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
+    const bool keep = ua >= ub;
+    fast_two_sum(keep ? a : b, keep ? b : a, s, e);
+}
+
+// x * 2^k exactly.  Exponent arithmetic on the bit pattern (no FP64 instruction) for
+// zero and for normal x whose result stays normal; a multiply otherwise.
+__device__ __forceinline__ double ldexp_exact(double x, int k)
+{
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (((unsigned long long)b << 1) == 0ULL) return x;
+    if (ex > 0 && ex + k > 0 && ex + k < 0x7ff) return __longlong_as_double(b + ((long long)k << 52));
+    return mul_(x, __longlong_as_double((long long)(1023 + k) << 52));
+}
+
 // p + e = a * b exactly (FMA).  2 FP64.
 __device__ __forceinline__ void two_prod(double a, double b, double &p, double &e)
 {
@@ -97,11 +119,13 @@ __device__ __forceinline__ R<1> r_add(R<1> a, R<1> b)  // 1 FP64
     r.v[0] = add_(a.v[0], b.v[0]);
     return r;
 }
-// double-double: two-sum of the leading limbs, lower limbs added into the error.  11 FP64.
+// double-double: two-sum of the leading limbs, lower limbs added into the error.  8 FP64.
+// Accepts an unnormalised operand (lower limb up to a few units in the last place of
+// the leading one); the result is normalised.
 __device__ __forceinline__ R<2> r_add(R<2> a, R<2> b)
 {
     double s, e;
-    two_sum(a.v[0], b.v[0], s, e);
+    two_sum_ord(a.v[0], b.v[0], s, e);
     e = add_(e, add_(a.v[1], b.v[1]));
     R<2> r;
     fast_two_sum(s, e, r.v[0], r.v[1]);
@@ -226,14 +250,15 @@ __device__ __forceinline__ R<4> r_div(R<4> a, R<4> b)
 }
 
 // ---------------------------------------------------------------- small integers
-// a * k for a small positive integer k; exact for powers of two.
+// a * k for a small positive integer k: exact for powers of two (exponent arithmetic,
+// no FP64 instruction), r_mul_d otherwise.
 template <int L> __device__ __forceinline__ R<L> r_scale_int(R<L> a, int k)
 {
     if (k == 1) return a;
     if ((k & (k - 1)) == 0) {
-        double s = (double)k;
+        const int e = __ffs(k) - 1;
 #pragma unroll
-        for (int j = 0; j < L; j++) a.v[j] = mul_(a.v[j], s);
+        for (int j = 0; j < L; j++) a.v[j] = ldexp_exact(a.v[j], e);
         return a;
     }
     return r_mul_d(a, (double)k);
@@ -301,9 +326,15 @@ template <> __device__ __forceinline__ C<1> c_mul<1>(C<1> a, C<1> b)
     return z;
 }
 // complex double-double, each part as ONE fused dot product of two DD products:
-// exact leading products, their difference by two-sum, all order-1 terms (product
+// exact leading products, their sum by an ordered two-sum, all order-1 terms (product
 // errors and the four cross terms) accumulated into the error by FMAs, one
-// renormalising fast-two-sum.  19 FP64 per part, 38 in all (50 for 4 mul + 2 add).
+// renormalising fast-two-sum.  16 FP64 per part, 32 in all (50 for 4 mul + 2 add).
+// Without the final renormalisation (NORM = false) the pair (s, e) is returned as is:
+// 13 per part, 26 in all.  Such an unnormalised value may only feed another product or an
+// addition (both renormalise): its lower limb is a few ulps of its leading limb, or after
+// cancellation a few ulps of the products' magnitude, so the normwise error stays at
+// 2^-106 of the terms' magnitude.
+template <bool NORM>
 __device__ __forceinline__ void dd_dot2(double a0, double a1, double b0, double b1,
                                         double c0, double c1, double d0, double d1,
                                         double &hi, double &lo)
@@ -312,21 +343,74 @@ __device__ __forceinline__ void dd_dot2(double a0, double a1, double b0, double 
     double p, q, ep, eq, s, e;
     two_prod(a0, b0, p, ep);
     two_prod(c0, d0, q, eq);
-    two_sum(p, q, s, e);
+    two_sum_ord(p, q, s, e);
     e = add_(e, add_(ep, eq));
     e = fma_(a0, b1, e);
     e = fma_(a1, b0, e);
     e = fma_(c0, d1, e);
     e = fma_(c1, d0, e);
-    fast_two_sum(s, e, hi, lo);
+    if (NORM) {
+        fast_two_sum(s, e, hi, lo);
+    } else {
+        hi = s;
+        lo = e;
+    }
 }
 template <> __device__ __forceinline__ C<2> c_mul<2>(C<2> a, C<2> b)
 {
     C<2> z;
-    dd_dot2(a.re.v[0], a.re.v[1], b.re.v[0], b.re.v[1],
-            -a.im.v[0], -a.im.v[1], b.im.v[0], b.im.v[1], z.re.v[0], z.re.v[1]);
-    dd_dot2(a.re.v[0], a.re.v[1], b.im.v[0], b.im.v[1],
-            a.im.v[0], a.im.v[1], b.re.v[0], b.re.v[1], z.im.v[0], z.im.v[1]);
+    dd_dot2<true>(a.re.v[0], a.re.v[1], b.re.v[0], b.re.v[1],
+                  -a.im.v[0], -a.im.v[1], b.im.v[0], b.im.v[1], z.re.v[0], z.re.v[1]);
+    dd_dot2<true>(a.re.v[0], a.re.v[1], b.im.v[0], b.im.v[1],
+                  a.im.v[0], a.im.v[1], b.re.v[0], b.re.v[1], z.im.v[0], z.im.v[1]);
+    return z;
+}
+
+// Product whose result only feeds another product or an addition: unnormalised in DD
+// (26 FP64), the plain product otherwise.
+template <int L> __device__ __forceinline__ C<L> c_mul_nn(C<L> a, C<L> b) { return c_mul(a, b); }
+template <> __device__ __forceinline__ C<2> c_mul_nn<2>(C<2> a, C<2> b)
+{
+    C<2> z;
+    dd_dot2<false>(a.re.v[0], a.re.v[1], b.re.v[0], b.re.v[1],
+                   -a.im.v[0], -a.im.v[1], b.im.v[0], b.im.v[1], z.re.v[0], z.re.v[1]);
+    dd_dot2<false>(a.re.v[0], a.re.v[1], b.im.v[0], b.im.v[1],
+                   a.im.v[0], a.im.v[1], b.re.v[0], b.re.v[1], z.im.v[0], z.im.v[1]);
+    return z;
+}
+
+// acc - l * b (the elimination update of Sec. 4); generic: product then subtraction.
+template <int L> __device__ __forceinline__ C<L> c_fnma(C<L> acc, C<L> l, C<L> b)
+{
+    return c_sub(acc, c_mul(l, b));
+}
+// DD: each part as one fused three-term sum a - (l.re b.re - l.im b.im) etc.  21 FP64
+// per part, 42 in all (48 for a product and a subtraction).
+__device__ __forceinline__ void dd_fnma_part(double a0, double a1, double x0, double x1, double y0,
+                                             double y1, double u0, double u1, double v0, double v1,
+                                             double &hi, double &lo)
+{
+    // a - x*y + u*v
+    double p, q, ep, eq, s, t, e1, e2;
+    two_prod(x0, y0, p, ep);
+    two_prod(u0, v0, q, eq);
+    two_sum_ord(a0, -p, s, e1);
+    two_sum_ord(s, q, t, e2);
+    double e = add_(add_(e1, e2), add_(a1, sub_(eq, ep)));
+    e = fma_(-x0, y1, e);
+    e = fma_(-x1, y0, e);
+    e = fma_(u0, v1, e);
+    e = fma_(u1, v0, e);
+    fast_two_sum(t, e, hi, lo);
+}
+template <> __device__ __forceinline__ C<2> c_fnma<2>(C<2> acc, C<2> l, C<2> b)
+{
+    C<2> z;
+    // re: acc.re - l.re b.re + l.im b.im ; im: acc.im - l.re b.im - l.im b.re
+    dd_fnma_part(acc.re.v[0], acc.re.v[1], l.re.v[0], l.re.v[1], b.re.v[0], b.re.v[1],
+                 l.im.v[0], l.im.v[1], b.im.v[0], b.im.v[1], z.re.v[0], z.re.v[1]);
+    dd_fnma_part(acc.im.v[0], acc.im.v[1], l.re.v[0], l.re.v[1], b.im.v[0], b.im.v[1],
+                 -l.im.v[0], -l.im.v[1], b.re.v[0], b.re.v[1], z.im.v[0], z.im.v[1]);
     return z;
 }
 

@@ -50,6 +50,9 @@ template <int L> __device__ __forceinline__ C<L> gamma_one_minus_t(double gre, d
 // the 3k-6 + k + 1 of the paper plus its k+1 coefficient products.  Then
 // Coefficient_Product (Alg. 4.1) reduces to f_i += value, J_{i,ij} += a_j D_j.
 // J is accumulated in place in the output buffer (this lane is its only writer).
+// Products inside the chain stay unnormalised (c_mul_nn); every addition renormalises,
+// and a pre[] entry with k == 1 (the common factor alone) also reaches J only through an
+// addition, so every stored value is normalised.
 //
 template <int L, bool JAC>
 __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool live, double t,
@@ -78,19 +81,19 @@ __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool liv
             for (int j = 0; j < k; j++) {
                 const int pk = __ldg(S.var_pack + q0 + j);
                 const int e = pk >> 16;
-                if (e >= 2) cf = c_mul(cf, V.pw(pk & 0xffff, e - 1));
+                if (e >= 2) cf = c_mul_nn(cf, V.pw(pk & 0xffff, e - 1));
             }
             if (!JAC) {
-                for (int j = 0; j < k; j++) cf = c_mul(cf, V.x(__ldg(S.var_pack + q0 + j) & 0xffff));
+                for (int j = 0; j < k; j++) cf = c_mul_nn(cf, V.x(__ldg(S.var_pack + q0 + j) & 0xffff));
                 fi = c_add(fi, cf);
                 continue;
             }
             // prefix products
             pre[0] = cf;
-            for (int j = 1; j < k; j++) pre[j] = c_mul(pre[j - 1], V.x(__ldg(S.var_pack + q0 + j - 1) & 0xffff));
+            for (int j = 1; j < k; j++) pre[j] = c_mul_nn(pre[j - 1], V.x(__ldg(S.var_pack + q0 + j - 1) & 0xffff));
             const int pk_last = __ldg(S.var_pack + q0 + k - 1);
             const C<L> xl = V.x(pk_last & 0xffff);
-            fi = c_add(fi, c_mul(pre[k - 1], xl));
+            fi = c_add(fi, c_mul_nn(pre[k - 1], xl));
             // backward sweep: D_j = pre_j * suf_j
             if (live) {
                 const size_t o = jrow + (size_t)(pk_last & 0xffff) * npts;
@@ -99,12 +102,12 @@ __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool liv
             C<L> suf = xl;
             for (int j = k - 2; j >= 0; j--) {
                 const int pk = __ldg(S.var_pack + q0 + j);
-                const C<L> d = c_scale_int(c_mul(pre[j], suf), pk >> 16);
+                const C<L> d = c_scale_int(c_mul_nn(pre[j], suf), pk >> 16);
                 if (live) {
                     const size_t o = jrow + (size_t)(pk & 0xffff) * npts;
                     st_c<L>(J, jplane, o, c_add(ld_c<L>(J, jplane, o), d));
                 }
-                if (j > 0) suf = c_mul(suf, V.x(pk & 0xffff));
+                if (j > 0) suf = c_mul_nn(suf, V.x(pk & 0xffff));
             }
         }
         if (t >= 0.0) {

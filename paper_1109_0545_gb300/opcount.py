@@ -12,18 +12,18 @@ from __future__ import annotations
 import numpy as np
 
 # FP64 instructions per operation, per limb count L
-C_MUL = {1: 4, 2: 38, 4: 4 * 107 + 2 * 80}
-C_ADD = {1: 2, 2: 22, 4: 2 * 80}
-R_ADD = {1: 1, 2: 11, 4: 80}
+C_MUL = {1: 4, 2: 32, 4: 4 * 107 + 2 * 80}      # normalised complex product
+C_MUL_NN = {1: 4, 2: 26, 4: 4 * 107 + 2 * 80}   # product feeding a product or a sum
+C_ADD = {1: 2, 2: 16, 4: 2 * 80}
+R_ADD = {1: 1, 2: 8, 4: 80}
 C_MUL_D = {1: 2, 2: 12, 4: 2 * 61}
 
 
 def scale_int(L: int, k: int) -> int:
-    """c_scale_int: free for 1, 2L DMULs per part for powers of two, else c_mul_d."""
-    if k == 1:
+    """c_scale_int: free for 1 and for powers of two (exponent arithmetic on the bit
+    pattern), c_mul_d otherwise."""
+    if k == 1 or k & (k - 1) == 0:
         return 0
-    if k & (k - 1) == 0:
-        return 2 * L
     return C_MUL_D[L]
 
 
@@ -36,7 +36,7 @@ def pow_mults(e: int) -> int:
 
 def eval_ops_per_point(s, L: int, homotopy: bool = True, jac: bool = True) -> int:
     """FP64 instructions of the evaluation kernel for one point of system ``s``."""
-    cm, ca = C_MUL[L], C_ADD[L]
+    cm, cn, ca = C_MUL[L], C_MUL_NN[L], C_ADD[L]
     total = 0
     vp, ve = s.var_ptr, s.var_exp
     for m in range(s.nmon):
@@ -47,10 +47,10 @@ def eval_ops_per_point(s, L: int, homotopy: bool = True, jac: bool = True) -> in
             continue
         n2 = int(np.sum(ex >= 2))
         if not jac:
-            total += (n2 + k) * cm + ca
+            total += (n2 + k) * cn + ca
             continue
         nmul = n2 + (3 * k - 3 if k >= 2 else 1)
-        total += nmul * cm + (k + 1) * ca + sum(scale_int(L, int(a)) for a in ex)
+        total += nmul * cn + (k + 1) * ca + sum(scale_int(L, int(a)) for a in ex)
     if homotopy:
         deg = np.zeros(s.npoly, dtype=np.int64)
         for i in range(s.npoly):
