@@ -134,6 +134,88 @@ int hc_newton_step(hc_system *sys, int npts, double t, double *x, int lu_mode,
  */
 int hc_set_tiles(int rows_per_task, int blocks_per_sm);
 
+/* predictors (Sec. 5) and tracker execution modes */
+#define HC_PRED_SECANT 0     /* linear through the last two accepted points */
+#define HC_PRED_QUADRATIC 1  /* per coordinate, the parabola through the last three */
+#define HC_TRACK_PERSISTENT 0  /* one persistent kernel, paths from an atomic queue */
+#define HC_TRACK_GRAPH 1       /* one stage per launch, replayed as a CUDA graph */
+
+/* Options of hc_track_path.  The paper gives no constants (Alg. 3.1); the defaults of
+ * hc_track_opts_default follow Tables 2-3: steps lambda0 * 2^j. */
+typedef struct {
+    double lambda0;     /* first step size, 0.01 */
+    double lambda_min;  /* stop (HC_MIN_STEP) once the step falls below this, 1e-12 */
+    double lambda_max;  /* largest step, 0.08 (= lambda0 * 2^3) */
+    double grow;        /* step factor after grow_after consecutive successes, 2 */
+    double shrink;      /* step factor after a failed corrector stage, 0.5 */
+    double eps;         /* corrector converged: ||h||_inf <= eps ...                */
+    double eps_x;       /*   ... or ||dz||_inf <= eps_x max(1, ||z||_inf)           */
+    double eps_end;     /* the same two tolerances for the end game at t = 1        */
+    double eps_end_x;
+    double div_bound;   /* ||z||_inf above this ends the path as HC_DIVERGED, 1e6 */
+    int32_t max_it;     /* Newton iterations per corrector stage, 3 */
+    int32_t end_it;     /* Newton iterations of the end game, 8 */
+    int32_t grow_after; /* consecutive successes before the step grows, 3 */
+    int32_t max_steps;  /* corrector stages before HC_MAX_STEPS, 100000 */
+    int32_t predictor;  /* HC_PRED_SECANT or HC_PRED_QUADRATIC */
+    int32_t lu_mode;    /* HC_LU_NATIVE or HC_LU_FP64_REFINE */
+    int32_t max_refine; /* refinement sweeps of HC_LU_FP64_REFINE, 4 */
+    int32_t mode;       /* HC_TRACK_PERSISTENT or HC_TRACK_GRAPH */
+    int32_t graph_steps;/* launches per graph in HC_TRACK_GRAPH, 16 */
+    int32_t reserved;
+} hc_track_opts;
+
+/* Per-path result (the statistics of Tables 2-3). */
+typedef struct {
+    int64_t n_succ;      /* successful corrector stages */
+    int64_t n_corr;      /* corrector stages */
+    int64_t newton_its;  /* Newton iterations along the path (end game excluded) */
+    double min_step, avg_step;  /* over accepted stages */
+    double t_end;        /* t reached */
+    double res_end;      /* residual of the last end-game iteration (-1: none) */
+    int32_t status;      /* HC_OK, HC_NOCONV, HC_SINGULAR, HC_MIN_STEP, ... */
+    int32_t end_its;     /* Newton iterations of the end game */
+} hc_path_stats;
+
+/* One corrector stage, as logged for the learned step-size proposer. */
+typedef struct {
+    double t;            /* t before the stage */
+    double lambda;       /* step attempted (t' - t) */
+    double res_first;    /* residual of the predicted point */
+    double res_last;     /* residual of the last Newton iterate evaluated */
+    double pc_dist;      /* ||corrected - predicted||_inf if accepted, else -1 */
+    double cond_log10;   /* log10 of max/min pivot modulus of the last factorisation */
+    int32_t iters;       /* Newton iterations */
+    int32_t accepted;    /* 1 if the stage was accepted */
+} hc_step_record;
+
+/* Fill *opts with the defaults listed above. */
+void hc_track_opts_default(hc_track_opts *opts);
+
+/*
+ * hc_track_path -- track npaths solution paths of h(x,t) = gamma (1-t) g(x) + t f(x),
+ * g_i = x_i^{d_i} - 1, from t = 0 to t = 1 (Alg. 3.1 with the Newton corrector of
+ * Alg. 4.1): predict at t' = min(t + lambda, 1), correct with at most max_it Newton
+ * iterations, accept (shift the history; grow lambda after grow_after successes) or
+ * step back (shrink lambda); stop on lambda < lambda_min, max_steps stages or
+ * ||z|| > div_bound; fail := (t < 1).  At t = 1 an end game of at most end_it Newton
+ * iterations on f.
+ *   sys    host array of npaths systems (each npoly == n <= 256, degrees >= 1, all
+ *          of one precision); path p runs on sys[p] (the same system may repeat)
+ *   x0     device, start points packed path after path, path p at offset
+ *          2 L (n_0 + ... + n_{p-1}) doubles as [2][L][n_p]
+ *   x1     device, end points in the same packing (caller-owned; may not alias x0)
+ *   stats  host, npaths results, valid on return
+ *   log    device, npaths * log_cap records (record s of path p at p * log_cap + s),
+ *          or NULL with log_cap = 0
+ * One thread block per path.  Synchronises the stream before returning.  Allocates and
+ * frees its own workspace.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA, HC_ETIMEOUT (graph
+ * mode only: paths still unfinished after max_steps / graph_steps + 2 replays).
+ */
+int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x1,
+                  const hc_track_opts *opts, hc_path_stats *stats, hc_step_record *log,
+                  int log_cap, void *stream);
+
 /* Message describing the last failure on the calling host thread ("" if none). */
 const char *hc_last_error(void);
 

@@ -20,6 +20,12 @@ struct DevSys {
     const double *coef;       // [nmon][2][L]
     const int32_t *deg;       // [npoly]
     double gre, gim;          // gamma
+    // tables of the block-per-path engine (hc_track_path)
+    const int32_t *perm;      // [nmon] monomials ordered by (k, number of exponents >= 2)
+    const int32_t *tptr;      // [npoly*(n+1)+1] contributions of entry (i, j), j == n is f_i
+    const int32_t *tlist;     // [nvar+nmon] slot in V of each contribution: var_ptr[m]+q for
+                              // the partial of monomial m in its q-th variable, nvar+m for
+                              // its value; original monomial order within an entry
 };
 
 struct hc_system {

@@ -199,15 +199,63 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     s->max_deg = max_deg;
     s->min_deg = min_deg;
 
-    // one device block: mon_ptr | var_ptr | var_pack | deg | coef (coef 256-aligned)
+    // tables of the block-per-path engine: monomials ordered by shape so the warps of a
+    // block walk monomials of equal length, and the transpose (entry -> contributions)
+    const int ne = npoly * (n + 1);
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (nmon > 0 ? nmon : 1));
+    int32_t *tptr = (int32_t *)calloc((size_t)ne + 1, sizeof(int32_t));
+    int32_t *tlist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nvar + nmon > 0 ? nvar + nmon : 1));
+    if (!perm || !tptr || !tlist) {
+        free(perm); free(tptr); free(tlist);
+        hc_system_free(s);
+        return hc_fail(HC_ENOMEM, "host allocation failed");
+    }
+    {
+        // counting sort by key = k * 64 + (exponents >= 2), stable
+        const int nkey = (HC_KMAX + 1) * 64;
+        int32_t *cnt = (int32_t *)calloc((size_t)nkey + 1, sizeof(int32_t));
+        if (!cnt) { free(perm); free(tptr); free(tlist); hc_system_free(s); return hc_fail(HC_ENOMEM, "host allocation failed"); }
+        auto key = [&](int m) {
+            int k = var_ptr[m + 1] - var_ptr[m], n2 = 0;
+            for (int q = var_ptr[m]; q < var_ptr[m + 1]; q++) n2 += var_exp[q] >= 2;
+            return k * 64 + n2;
+        };
+        for (int m = 0; m < nmon; m++) cnt[key(m) + 1]++;
+        for (int k = 0; k < nkey; k++) cnt[k + 1] += cnt[k];
+        for (int m = 0; m < nmon; m++) perm[cnt[key(m)]++] = m;
+        free(cnt);
+        // transpose: count, prefix, fill in monomial order
+        for (int i = 0; i < npoly; i++)
+            for (int m = mon_ptr[i]; m < mon_ptr[i + 1]; m++) {
+                tptr[i * (n + 1) + n + 1]++;
+                for (int q = var_ptr[m]; q < var_ptr[m + 1]; q++) tptr[i * (n + 1) + var_idx[q] + 1]++;
+            }
+        for (int e = 0; e < ne; e++) tptr[e + 1] += tptr[e];
+        int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ne > 0 ? ne : 1));
+        if (!fill) { free(perm); free(tptr); free(tlist); hc_system_free(s); return hc_fail(HC_ENOMEM, "host allocation failed"); }
+        memcpy(fill, tptr, sizeof(int32_t) * (size_t)ne);
+        for (int i = 0; i < npoly; i++)
+            for (int m = mon_ptr[i]; m < mon_ptr[i + 1]; m++) {
+                tlist[fill[i * (n + 1) + n]++] = nvar + m;
+                for (int q = var_ptr[m]; q < var_ptr[m + 1]; q++)
+                    tlist[fill[i * (n + 1) + var_idx[q]]++] = q;
+            }
+        free(fill);
+    }
+
+    // one device block: mon_ptr | var_ptr | var_pack | deg | perm | tptr | tlist | coef
     size_t o_mon = 0;
     size_t o_var = hc_align256(o_mon + sizeof(int32_t) * (npoly + 1));
     size_t o_pack = hc_align256(o_var + sizeof(int32_t) * (nmon + 1));
     size_t o_deg = hc_align256(o_pack + sizeof(int32_t) * (nvar > 0 ? nvar : 1));
-    size_t o_coef = hc_align256(o_deg + sizeof(int32_t) * npoly);
+    size_t o_perm = hc_align256(o_deg + sizeof(int32_t) * npoly);
+    size_t o_tptr = hc_align256(o_perm + sizeof(int32_t) * (nmon > 0 ? nmon : 1));
+    size_t o_tlist = hc_align256(o_tptr + sizeof(int32_t) * ((size_t)ne + 1));
+    size_t o_coef = hc_align256(o_tlist + sizeof(int32_t) * (size_t)(nvar + nmon > 0 ? nvar + nmon : 1));
     size_t total = hc_align256(o_coef + sizeof(double) * 2 * prec * (size_t)(nmon > 0 ? nmon : 1));
     cudaError_t e = cudaMalloc(&s->dev_block, total);
     if (e != cudaSuccess) {
+        free(perm); free(tptr); free(tlist);
         hc_system_free(s);
         return hc_cuda_fail(e, "cudaMalloc(system tables)");
     }
@@ -216,8 +264,15 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     if (e == cudaSuccess) e = cudaMemcpy(b + o_var, s->h_var_ptr, sizeof(int32_t) * (nmon + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nvar > 0) e = cudaMemcpy(b + o_pack, s->h_var_pack, sizeof(int32_t) * nvar, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + o_deg, s->h_deg, sizeof(int32_t) * npoly, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nmon > 0) e = cudaMemcpy(b + o_perm, perm, sizeof(int32_t) * nmon, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_tptr, tptr, sizeof(int32_t) * ((size_t)ne + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nvar + nmon > 0)
+        e = cudaMemcpy(b + o_tlist, tlist, sizeof(int32_t) * (size_t)(nvar + nmon), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nmon > 0)
         e = cudaMemcpy(b + o_coef, coef, sizeof(double) * 2 * prec * (size_t)nmon, cudaMemcpyHostToDevice);
+    free(perm);
+    free(tptr);
+    free(tlist);
     if (e != cudaSuccess) {
         hc_system_free(s);
         return hc_cuda_fail(e, "cudaMemcpy(system tables)");
@@ -232,6 +287,9 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     d.var_ptr = (const int32_t *)(b + o_var);
     d.var_pack = (const int32_t *)(b + o_pack);
     d.deg = (const int32_t *)(b + o_deg);
+    d.perm = (const int32_t *)(b + o_perm);
+    d.tptr = (const int32_t *)(b + o_tptr);
+    d.tlist = (const int32_t *)(b + o_tlist);
     d.coef = (const double *)(b + o_coef);
     d.gre = gamma[0];
     d.gim = gamma[1];

@@ -1,0 +1,471 @@
+// hc_track.cu -- hc_track_path: the path tracker of Alg. 3.1 (predictor, Newton corrector
+// of Alg. 4.1, step-size control, step back, stop criterion) for many paths of uneven
+// dimension, each on its own system, one thread block per path.
+//
+// Two ways to run it:
+//   HC_TRACK_PERSISTENT  one persistent kernel; each block takes paths from an atomic
+//                        queue and tracks each to its end;
+//   HC_TRACK_GRAPH       every launch advances each unfinished path by one
+//                        predictor-corrector stage; the host replays a CUDA graph of
+//                        several such launches until no path is left.
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "path.cuh"
+
+namespace hc {
+
+struct PathState {
+    double t, tp, tpp, lambda, minstep, sumstep, res_end, pad;
+    long long n_succ, n_corr, nits;
+    int nhist, consec, status, phase;  // phase: 0 new, 1 tracking, 2 end game, 3 done
+    int end_its, pad2;
+};
+
+struct SlotLayout {
+    size_t pw, v, h, jh, b, rv, dz, zp, piv, stride;
+};
+
+struct TrackArgs {
+    const DevSys *sys;        // [npaths]
+    const long long *xoff;    // [npaths] offset (doubles) of path p in x0/x1
+    const double *x0;
+    double *x1;
+    double *vecs;             // per path: previous, second previous, predicted+corrected
+    PathState *st;
+    hc_track_opts o;
+    char *slots;
+    SlotLayout lay;
+    int *queue;
+    int *active;
+    hc_step_record *log;
+    int log_cap;
+    int npaths;
+};
+
+template <int L> __device__ __forceinline__ Slot<L> slot_of(const TrackArgs &a, int b)
+{
+    char *base = a.slots + (size_t)b * a.lay.stride;
+    Slot<L> w;
+    w.PW = (double *)(base + a.lay.pw);
+    w.V = (double *)(base + a.lay.v);
+    w.H = (double *)(base + a.lay.h);
+    w.JH = (double *)(base + a.lay.jh);
+    w.B = (double *)(base + a.lay.b);
+    w.RV = (double *)(base + a.lay.rv);
+    w.DZ = (double *)(base + a.lay.dz);
+    w.ZP = (double *)(base + a.lay.zp);
+    w.PIV = (int32_t *)(base + a.lay.piv);
+    return w;
+}
+
+// ||v||_inf from the leading limbs, the same value on every thread
+template <int L> __device__ __forceinline__ double vec_norm(int n, const double *v, BlockShared &sh)
+{
+    double m = 0.0;
+    for (int j = threadIdx.x; j < n; j += HC_TB) m = fmax(m, sqrt(c_abs2_lead(ld_c<L>(v, n, j))));
+    return block_max(m, sh);
+}
+
+//
+// Advance path p by at most max_stages corrector stages (then its end game, once t = 1).
+// Every thread keeps the same copy of the path's scalars: each decision is taken from
+// values that block reductions broadcast, so all threads follow the same branch.
+//
+template <int L>
+__device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShared &sh, int max_stages)
+{
+    const DevSys S = a.sys[p];
+    const hc_track_opts &o = a.o;
+    const int n = S.n, tid = threadIdx.x;
+    double *z = a.x1 + a.xoff[p];
+    double *zp = a.vecs + 3 * a.xoff[p];
+    double *zpp = zp + 2 * L * n;
+    double *zh = zpp + 2 * L * n;
+    PathState st = a.st[p];
+    if (st.phase == 3) return;
+    if (st.phase == 0) {
+        for (int q = tid; q < 2 * L * n; q += HC_TB) z[q] = a.x0[a.xoff[p] + q];
+        st.t = st.tp = st.tpp = 0.0;
+        st.lambda = o.lambda0;
+        st.minstep = INFINITY;
+        st.sumstep = 0.0;
+        st.res_end = -1.0;
+        st.n_succ = st.n_corr = st.nits = 0;
+        st.nhist = 1;
+        st.consec = 0;
+        st.status = HC_OK;
+        st.phase = 1;
+        st.end_its = 0;
+        __syncthreads();
+    }
+    int stages = 0;
+    while (st.phase == 1 && stages < max_stages) {
+        double t1 = add_(st.t, st.lambda);
+        if (t1 > 1.0) t1 = 1.0;
+        const double h = sub_(t1, st.t);
+        // predictor (Alg. 3.1 "predict"; Sec. 5 for the quadratic one)
+        if (o.predictor == HC_PRED_QUADRATIC && st.nhist >= 3) {
+            const double w0 = __ddiv_rn(mul_(sub_(t1, st.tp), sub_(t1, st.t)), mul_(sub_(st.tpp, st.tp), sub_(st.tpp, st.t)));
+            const double w1 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.t)), mul_(sub_(st.tp, st.tpp), sub_(st.tp, st.t)));
+            const double w2 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.tp)), mul_(sub_(st.t, st.tpp), sub_(st.t, st.tp)));
+            for (int j = tid; j < n; j += HC_TB) {
+                const C<L> v = c_add(c_add(c_mul_d(ld_c<L>(zpp, n, j), w0), c_mul_d(ld_c<L>(zp, n, j), w1)),
+                                     c_mul_d(ld_c<L>(z, n, j), w2));
+                st_c<L>(zh, n, j, v);
+                st_c<L>(w.ZP, n, j, v);
+            }
+        } else if (st.nhist >= 2) {
+            const double r = __ddiv_rn(h, sub_(st.t, st.tp));
+            for (int j = tid; j < n; j += HC_TB) {
+                const C<L> zj = ld_c<L>(z, n, j);
+                const C<L> v = c_add(zj, c_mul_d(c_sub(zj, ld_c<L>(zp, n, j)), r));
+                st_c<L>(zh, n, j, v);
+                st_c<L>(w.ZP, n, j, v);
+            }
+        } else {
+            for (int j = tid; j < n; j += HC_TB) {
+                const C<L> v = ld_c<L>(z, n, j);
+                st_c<L>(zh, n, j, v);
+                st_c<L>(w.ZP, n, j, v);
+            }
+        }
+        __syncthreads();
+        // corrector: Alg. 4.1
+        double res = 1.0, res_first = -1.0, cond = 0.0;
+        int it = 0, nst = HC_OK, conv = 0;
+        while (!conv && it < o.max_it) {
+            const NewtonOut no = block_newton<L>(S, zh, t1, o.lu_mode, o.max_refine, w, sh);
+            res = no.res;
+            if (res_first < 0) res_first = res;
+            it++;
+            nst = no.status;
+            cond = no.cond;
+            if (nst != HC_OK) break;
+            conv = (res <= o.eps) || (no.dzn <= o.eps_x * (no.zn > 1.0 ? no.zn : 1.0));
+        }
+        st.nits += it;
+        st.n_corr++;
+        int ok = (nst == HC_OK) && conv;
+        const double znorm = vec_norm<L>(n, zh, sh);
+        int stop = 0;
+        if (ok && !(znorm <= o.div_bound)) {
+            ok = 0;
+            st.status = isfinite(znorm) ? HC_DIVERGED : HC_NONFINITE;
+            stop = 1;
+        }
+        double pcd = -1.0;
+        if (ok) {
+            double m = 0.0;
+            for (int j = tid; j < n; j += HC_TB)
+                m = fmax(m, sqrt(c_abs2_lead(c_sub(ld_c<L>(zh, n, j), ld_c<L>(w.ZP, n, j)))));
+            pcd = block_max(m, sh);
+        }
+        if (a.log && tid == 0 && st.n_corr <= a.log_cap) {
+            hc_step_record &r = a.log[(size_t)p * a.log_cap + (st.n_corr - 1)];
+            r.t = st.t;
+            r.lambda = h;
+            r.res_first = res_first;
+            r.res_last = res;
+            r.pc_dist = pcd;
+            r.cond_log10 = cond;
+            r.iters = it;
+            r.accepted = ok;
+        }
+        if (ok) {
+            for (int j = tid; j < n; j += HC_TB) {
+                st_c<L>(zpp, n, j, ld_c<L>(zp, n, j));
+                st_c<L>(zp, n, j, ld_c<L>(z, n, j));
+                st_c<L>(z, n, j, ld_c<L>(zh, n, j));
+            }
+            st.tpp = st.tp;
+            st.tp = st.t;
+            st.t = t1;
+            if (st.nhist < 3) st.nhist++;
+            st.n_succ++;
+            st.sumstep = add_(st.sumstep, h);
+            if (h < st.minstep) st.minstep = h;
+            st.consec++;
+            if (st.consec >= o.grow_after) {
+                st.lambda = mul_(st.lambda, o.grow);
+                if (st.lambda > o.lambda_max) st.lambda = o.lambda_max;
+                st.consec = 0;
+            }
+        } else if (!stop) {
+            st.consec = 0;
+            st.lambda = mul_(st.lambda, o.shrink);
+            if (st.lambda < o.lambda_min) {
+                stop = 1;
+                st.status = HC_MIN_STEP;
+            }
+        }
+        if (!stop && st.t < 1.0 && st.n_corr >= o.max_steps) {
+            stop = 1;
+            st.status = HC_MAX_STEPS;
+        }
+        __syncthreads();
+        if (stop)
+            st.phase = 3;
+        else if (st.t >= 1.0)
+            st.phase = 2;
+        stages++;
+    }
+    if (st.phase == 2) {
+        // end game at t = 1: Newton on f until converged with the end tolerances
+        double res = 1.0;
+        int conv = 0;
+        while (!conv && st.end_its < o.end_it) {
+            const NewtonOut no = block_newton<L>(S, z, 1.0, o.lu_mode, o.max_refine, w, sh);
+            st.end_its++;
+            res = no.res;
+            if (no.status != HC_OK) {
+                st.status = no.status;
+                break;
+            }
+            conv = (res <= o.eps_end) || (no.dzn <= o.eps_end_x * (no.zn > 1.0 ? no.zn : 1.0));
+        }
+        st.res_end = res;
+        if (st.status == HC_OK && !conv) st.status = HC_NOCONV;
+        st.phase = 3;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        a.st[p] = st;
+        if (st.phase == 3) atomicSub(a.active, 1);
+    }
+    __syncthreads();
+}
+
+template <int L>
+__global__ void __launch_bounds__(HC_TB) k_track(TrackArgs a, int persistent)
+{
+    __shared__ BlockShared sh;
+    __shared__ int s_p;
+    const Slot<L> w = slot_of<L>(a, blockIdx.x);
+    if (persistent) {
+        for (;;) {
+            if (threadIdx.x == 0) s_p = atomicAdd(a.queue, 1);
+            __syncthreads();
+            const int p = s_p;
+            __syncthreads();
+            if (p >= a.npaths) break;
+            path_run<L>(a, p, w, sh, 0x7fffffff);
+        }
+    } else {
+        for (int p = blockIdx.x; p < a.npaths; p += gridDim.x) path_run<L>(a, p, w, sh, 1);
+    }
+}
+
+}  // namespace hc
+
+using namespace hc;
+
+extern "C" void hc_track_opts_default(hc_track_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->lambda0 = 0.01;
+    o->lambda_min = 1e-12;
+    o->lambda_max = 0.08;
+    o->grow = 2.0;
+    o->shrink = 0.5;
+    o->eps = 1e-26;
+    o->eps_x = 1e-8;
+    o->eps_end = 1e-26;
+    o->eps_end_x = 1e-26;
+    o->div_bound = 1e6;
+    o->max_it = 3;
+    o->end_it = 8;
+    o->grow_after = 3;
+    o->max_steps = 100000;
+    o->predictor = HC_PRED_SECANT;
+    o->lu_mode = HC_LU_NATIVE;
+    o->max_refine = 4;
+    o->mode = HC_TRACK_PERSISTENT;
+    o->graph_steps = 16;
+}
+
+static int check_opts(const hc_track_opts *o)
+{
+    if (!o) return hc_fail(HC_EINVAL, "opts is NULL");
+    if (!(o->lambda0 > 0) || !(o->lambda_min > 0) || !(o->lambda_max >= o->lambda0))
+        return hc_fail(HC_EINVAL, "step sizes must satisfy 0 < lambda_min, 0 < lambda0 <= lambda_max");
+    if (!(o->grow >= 1.0) || !(o->shrink > 0.0 && o->shrink < 1.0))
+        return hc_fail(HC_EINVAL, "need grow >= 1 and 0 < shrink < 1");
+    if (o->max_it < 1 || o->end_it < 0 || o->grow_after < 1 || o->max_steps < 1)
+        return hc_fail(HC_EINVAL, "need max_it >= 1, end_it >= 0, grow_after >= 1, max_steps >= 1");
+    if (o->predictor != HC_PRED_SECANT && o->predictor != HC_PRED_QUADRATIC)
+        return hc_fail(HC_EINVAL, "unknown predictor %d", o->predictor);
+    if (o->lu_mode != HC_LU_NATIVE && o->lu_mode != HC_LU_FP64_REFINE)
+        return hc_fail(HC_EINVAL, "unknown lu_mode %d", o->lu_mode);
+    if (o->lu_mode == HC_LU_FP64_REFINE && (o->max_refine < 1 || o->max_refine > 64))
+        return hc_fail(HC_EINVAL, "max_refine out of [1, 64]");
+    if (o->mode != HC_TRACK_PERSISTENT && o->mode != HC_TRACK_GRAPH)
+        return hc_fail(HC_EINVAL, "unknown mode %d", o->mode);
+    if (o->mode == HC_TRACK_GRAPH && (o->graph_steps < 1 || o->graph_steps > 1024))
+        return hc_fail(HC_EINVAL, "graph_steps out of [1, 1024]");
+    return HC_SUCCESS;
+}
+
+template <int L>
+static int launch_track(TrackArgs &a, int grid, int persistent, cudaStream_t st)
+{
+    k_track<L><<<grid, HC_TB, 0, st>>>(a, persistent);
+    return HC_SUCCESS;
+}
+
+template <int L> static int occupancy_track()
+{
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_track<L>, HC_TB, 0);
+    return occ < 1 ? 1 : occ;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x1,
+                             const hc_track_opts *opts, hc_path_stats *stats, hc_step_record *log,
+                             int log_cap, void *stream)
+{
+    if (!sys || npaths < 1) return hc_fail(HC_EINVAL, "need npaths >= 1 systems");
+    if (!x0 || !x1 || !stats) return hc_fail(HC_EINVAL, "x0, x1 or stats is NULL");
+    if (log_cap < 0 || (log_cap > 0 && !log)) return hc_fail(HC_EINVAL, "bad log buffer");
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    int L = 0, nmax = 0, emax = 1;
+    long long vmax = 0, total = 0;
+    std::vector<DevSys> hs((size_t)npaths);
+    std::vector<long long> off((size_t)npaths);
+    for (int p = 0; p < npaths; p++) {
+        const hc_system *s = sys[p];
+        if (!s) return hc_fail(HC_EINVAL, "system %d is NULL", p);
+        if (p == 0) L = s->prec;
+        if (s->prec != L) return hc_fail(HC_EINVAL, "systems of different precision");
+        if (s->npoly != s->n) return hc_fail(HC_EINVAL, "system %d: tracking needs npoly == n", p);
+        if (s->min_deg < 1) return hc_fail(HC_EINVAL, "system %d: a polynomial of degree 0", p);
+        if (s->n > 256) return hc_fail(HC_EINVAL, "system %d: n = %d above the tracker's 256", p, s->n);
+        hs[p] = s->dev;
+        off[p] = total;
+        total += 2LL * L * s->n;
+        nmax = s->n > nmax ? s->n : nmax;
+        emax = s->max_exp > emax ? s->max_exp : emax;
+        const long long v = (long long)s->nvar + s->nmon;
+        vmax = v > vmax ? v : vmax;
+    }
+    const int sms = hc_num_sms();
+    int occ = L == 1 ? occupancy_track<1>() : L == 2 ? occupancy_track<2>() : occupancy_track<4>();
+    const int grid = (int)(npaths < (long long)sms * occ ? npaths : (long long)sms * occ);
+
+    SlotLayout lay;
+    size_t o = 0;
+    auto put = [&](size_t bytes) { size_t at = o; o = hc_align256(o + bytes); return at; };
+    lay.pw = put(sizeof(double) * 2 * L * (size_t)nmax * (emax > 2 ? emax - 2 : 1));
+    lay.v = put(sizeof(double) * 2 * L * (size_t)(vmax > 0 ? vmax : 1));
+    lay.h = put(sizeof(double) * 2 * L * (size_t)nmax);
+    lay.jh = put(sizeof(double) * 2 * L * (size_t)nmax * nmax);
+    lay.b = put(sizeof(double) * 2 * (size_t)nmax * nmax);
+    lay.rv = put(sizeof(double) * 2 * (size_t)nmax);
+    lay.dz = put(sizeof(double) * 2 * L * (size_t)nmax);
+    lay.zp = put(sizeof(double) * 2 * L * (size_t)nmax);
+    lay.piv = put(sizeof(int32_t) * (size_t)nmax);
+    lay.stride = o;
+
+    size_t b_sys = hc_align256(sizeof(DevSys) * npaths);
+    size_t b_off = hc_align256(sizeof(long long) * npaths);
+    size_t b_vec = hc_align256(sizeof(double) * 3 * (size_t)total);
+    size_t b_st = hc_align256(sizeof(PathState) * npaths);
+    size_t b_ctr = 256;
+    size_t bytes = b_sys + b_off + b_vec + b_st + b_ctr + lay.stride * (size_t)grid;
+    DevBuf ws;
+    HC_CUDA_TRY(cudaMalloc(&ws.p, bytes));
+    char *b = (char *)ws.p;
+    cudaStream_t st = (cudaStream_t)stream;
+    TrackArgs a;
+    a.sys = (const DevSys *)b;
+    a.xoff = (const long long *)(b + b_sys);
+    a.vecs = (double *)(b + b_sys + b_off);
+    a.st = (PathState *)(b + b_sys + b_off + b_vec);
+    int *ctr = (int *)(b + b_sys + b_off + b_vec + b_st);
+    a.queue = ctr;
+    a.active = ctr + 1;
+    a.slots = b + b_sys + b_off + b_vec + b_st + b_ctr;
+    a.lay = lay;
+    a.x0 = x0;
+    a.x1 = x1;
+    a.o = *opts;
+    a.log = log_cap > 0 ? log : nullptr;
+    a.log_cap = log_cap;
+    a.npaths = npaths;
+    HC_CUDA_TRY(cudaMemcpyAsync((void *)a.sys, hs.data(), sizeof(DevSys) * npaths, cudaMemcpyHostToDevice, st));
+    HC_CUDA_TRY(cudaMemcpyAsync((void *)a.xoff, off.data(), sizeof(long long) * npaths, cudaMemcpyHostToDevice, st));
+    HC_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(PathState) * npaths, st));
+    int hctr[2] = {0, npaths};
+    HC_CUDA_TRY(cudaMemcpyAsync(ctr, hctr, sizeof hctr, cudaMemcpyHostToDevice, st));
+
+    if (opts->mode == HC_TRACK_PERSISTENT) {
+        if (L == 1) launch_track<1>(a, grid, 1, st);
+        else if (L == 2) launch_track<2>(a, grid, 1, st);
+        else launch_track<4>(a, grid, 1, st);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return hc_cuda_fail(e, "k_track launch");
+    } else {
+        // one predictor-corrector stage per launch, graph_steps launches per graph
+        cudaStream_t cs;
+        HC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaEvent_t ready;
+        cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        cudaEventRecord(ready, st);
+        cudaStreamWaitEvent(cs, ready, 0);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int g = 0; g < opts->graph_steps; g++) {
+                if (L == 1) launch_track<1>(a, grid, 0, cs);
+                else if (L == 2) launch_track<2>(a, grid, 0, cs);
+                else launch_track<4>(a, grid, 0, cs);
+            }
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        int h_active = npaths;
+        // every stage either accepts, halves the step or ends the path, so a path ends
+        // within max_steps stages (plus its end game, taken in the same launch)
+        const long long max_replays = (long long)opts->max_steps / opts->graph_steps + 2;
+        for (long long r = 0; e == cudaSuccess && r < max_replays && h_active > 0; r++) {
+            e = cudaGraphLaunch(exec, cs);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, a.active, sizeof(int), cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaEventRecord(ready, cs);
+        cudaStreamWaitEvent(st, ready, 0);
+        cudaEventDestroy(ready);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return hc_cuda_fail(e, "graph-stepped tracking");
+        if (h_active > 0) return hc_fail(HC_ETIMEOUT, "%d paths unfinished after the replay limit", h_active);
+    }
+    std::vector<PathState> hst((size_t)npaths);
+    HC_CUDA_TRY(cudaMemcpyAsync(hst.data(), a.st, sizeof(PathState) * npaths, cudaMemcpyDeviceToHost, st));
+    HC_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int p = 0; p < npaths; p++) {
+        const PathState &q = hst[p];
+        hc_path_stats &r = stats[p];
+        r.n_succ = q.n_succ;
+        r.n_corr = q.n_corr;
+        r.newton_its = q.nits;
+        r.min_step = q.n_succ ? q.minstep : 0.0;
+        r.avg_step = q.n_succ ? q.sumstep / (double)q.n_succ : 0.0;
+        r.t_end = q.t;
+        r.res_end = q.res_end;
+        r.status = q.status;
+        r.end_its = q.end_its;
+    }
+    return HC_SUCCESS;
+}

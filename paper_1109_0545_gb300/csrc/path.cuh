@@ -1,0 +1,461 @@
+// path.cuh -- one thread block per path: evaluation of h and its Jacobian at one point of
+// the path's own system, and the Newton corrector of Alg. 4.1 on it, block-cooperative.
+// Used by the path tracker (hc_track.cu).
+#pragma once
+#include "points.cuh"
+
+namespace hc {
+
+#define HC_TB 128          // threads per path block
+#define HC_TW (HC_TB / 32)
+
+// per-slot scratch of one block (global memory, sized for the largest system)
+template <int L> struct Slot {
+    double *PW;    // [max_exp-2][2][L][n]
+    double *V;     // [2][L][nvar+nmon] (plane = nvar+nmon): partials, then values
+    double *H;     // [2][L][n]
+    double *JH;    // [2][L][n][n]
+    double *B;     // [2][n][n] FP64 factors
+    double *RV;    // [2][n]
+    double *DZ;    // [2][L][n]
+    double *ZP;    // [2][L][n] the predicted point of the current stage
+    int32_t *PIV;  // [n]
+};
+
+struct BlockShared {
+    double rv[HC_TW];
+    int ri[HC_TW];
+    double bc[4];
+    int ibc[4];
+};
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// max over the block; every thread gets the same value
+__device__ __forceinline__ double block_max(double v, BlockShared &sh)
+{
+    v = warp_max(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh.rv[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double m = sh.rv[0];
+#pragma unroll
+    for (int w = 1; w < HC_TW; w++) m = fmax(m, sh.rv[w]);
+    return m;
+}
+
+__device__ __forceinline__ int block_and(int v, BlockShared &sh)
+{
+    return __syncthreads_and(v);
+}
+
+// argmax of (v, i) over the block, ties to the lowest i; every thread gets the winner
+__device__ __forceinline__ void block_argmax(double &v, int &i, BlockShared &sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (v2 > v || (v2 == v && i2 < i)) {
+            v = v2;
+            i = i2;
+        }
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh.rv[threadIdx.x >> 5] = v;
+        sh.ri[threadIdx.x >> 5] = i;
+    }
+    __syncthreads();
+    v = sh.rv[0];
+    i = sh.ri[0];
+#pragma unroll
+    for (int w = 1; w < HC_TW; w++)
+        if (sh.rv[w] > v || (sh.rv[w] == v && sh.ri[w] < i)) {
+            v = sh.rv[w];
+            i = sh.ri[w];
+        }
+}
+
+// ------------------------------------------------------------------------------ evaluation
+//
+// h(z, t) (t >= 0) or f(z) (t < 0) and the Jacobian at one point z[2][L][n], into
+// w.H[2][L][n] and w.JH[2][L][n][n].  Two phases:
+//   1. monomial-parallel, over the monomials in shape order (so a warp's monomials have
+//      equal length): the common factor with the coefficient folded in, prefix products
+//      and the backward sweep of points.cuh give each monomial's value c x^a and its
+//      scaled partials a_j c x^(a - e_j), stored in V;
+//   2. entry-parallel: each thread owns entries (i, j) and adds their contributions in
+//      the original monomial order (transpose table), then assembles the homotopy.
+//
+template <int L>
+__device__ void block_eval(const DevSys &S, const double *__restrict__ z, double t, const Slot<L> &w)
+{
+    const int n = S.n, tid = threadIdx.x;
+    const size_t vplane = (size_t)S.nvar + S.nmon;
+    for (int j = tid; j < n; j += HC_TB) {
+        const C<L> x = ld_c<L>(z, n, j);
+        C<L> v = x;
+        for (int e = 2; e < S.max_exp; e++) {
+            v = c_mul(v, x);
+            st_c<L>(w.PW + (size_t)(e - 2) * 2 * L * n, n, j, v);
+        }
+    }
+    __syncthreads();
+    auto X = [&](int j) { return ld_c<L>(z, n, j); };
+    auto P = [&](int j, int e) { return e == 1 ? X(j) : ld_c<L>(w.PW + (size_t)(e - 2) * 2 * L * n, n, j); };
+    C<L> pre[HC_KLOCAL];
+    for (int q = tid; q < S.nmon; q += HC_TB) {
+        const int m = __ldg(S.perm + q);
+        const int q0 = __ldg(S.var_ptr + m), k = __ldg(S.var_ptr + m + 1) - q0;
+        const C<L> c = ld_c<L>(S.coef + (size_t)m * 2 * L, 1, 0);
+        if (k == 0) {
+            st_c<L>(w.V, vplane, (size_t)S.nvar + m, c);
+            continue;
+        }
+        C<L> cf = c;
+        for (int j = 0; j < k; j++) {
+            const int pk = __ldg(S.var_pack + q0 + j);
+            if ((pk >> 16) >= 2) cf = c_mul_nn(cf, P(pk & 0xffff, (pk >> 16) - 1));
+        }
+        pre[0] = cf;
+        for (int j = 1; j < k; j++) pre[j] = c_mul_nn(pre[j - 1], X(__ldg(S.var_pack + q0 + j - 1) & 0xffff));
+        const int pkl = __ldg(S.var_pack + q0 + k - 1);
+        const C<L> xl = X(pkl & 0xffff);
+        st_c<L>(w.V, vplane, (size_t)S.nvar + m, c_mul_nn(pre[k - 1], xl));
+        st_c<L>(w.V, vplane, (size_t)q0 + k - 1, c_scale_int(pre[k - 1], pkl >> 16));
+        C<L> suf = xl;
+        for (int j = k - 2; j >= 0; j--) {
+            const int pk = __ldg(S.var_pack + q0 + j);
+            st_c<L>(w.V, vplane, (size_t)q0 + j, c_scale_int(c_mul_nn(pre[j], suf), pk >> 16));
+            if (j > 0) suf = c_mul_nn(suf, X(pk & 0xffff));
+        }
+    }
+    __syncthreads();
+    const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
+    const int ne = S.npoly * (n + 1);
+    for (int e = tid; e < ne; e += HC_TB) {
+        const int i = e / (n + 1), j = e - i * (n + 1);
+        C<L> acc = c_zero<L>();
+        const int r1 = __ldg(S.tptr + e + 1);
+        for (int r = __ldg(S.tptr + e); r < r1; r++) acc = c_add(acc, ld_c<L>(w.V, vplane, __ldg(S.tlist + r)));
+        if (t >= 0.0) {
+            const int d = __ldg(S.deg + i);
+            if (j == n) {
+                const C<L> xi = X(i);
+                C<L> g = c_mul(c_pow(xi, d - 1), xi);
+                g.re = r_sub(g.re, r_from<L>(1.0));
+                acc = c_add(c_mul(gs, g), c_mul_d(acc, t));
+            } else {
+                acc = c_mul_d(acc, t);
+                if (i == j) acc = c_add(acc, c_mul(gs, c_scale_int(c_pow(X(i), d - 1), d)));
+            }
+        }
+        if (j == n)
+            st_c<L>(w.H, n, i, acc);
+        else
+            st_c<L>(w.JH, (size_t)n * n, (size_t)i * n + j, acc);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------ solves
+// Elimination with partial pivoting on [A b] in the working precision (Sec. 4), block
+// version: the pivot is the entry of largest leading-limb |.|^2 (ties to the lowest row),
+// rows are swapped, the pivot's reciprocal replaces it, multipliers replace the column
+// below it, the trailing block and b are updated; back substitution leaves z = A^-1 b in b.
+// *cond gets log10 of the ratio of the largest to the smallest pivot modulus.
+template <int L>
+__device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, BlockShared &sh, double *cond)
+{
+    const int tid = threadIdx.x;
+    const size_t ap = (size_t)n * n;
+    double pmax = 0.0, pmin = INFINITY;
+    for (int k = 0; k < n; k++) {
+        double bv = -1.0;
+        int bi = 0x7fffffff;
+        for (int i = k + tid; i < n; i += HC_TB) {
+            const C<L> a = ld_c<L>(A, ap, (size_t)i * n + k);
+            const double v = c_abs2_lead(a);
+            if (v > bv) {
+                bv = v;
+                bi = i;
+            }
+        }
+        block_argmax(bv, bi, sh);
+        if (!(bv > 0.0)) return HC_SINGULAR;
+        pmax = fmax(pmax, bv);
+        pmin = fmin(pmin, bv);
+        const int piv = bi;
+        if (piv != k) {
+            for (int j = k + tid; j < n; j += HC_TB) {
+                const C<L> t0 = ld_c<L>(A, ap, (size_t)k * n + j);
+                st_c<L>(A, ap, (size_t)k * n + j, ld_c<L>(A, ap, (size_t)piv * n + j));
+                st_c<L>(A, ap, (size_t)piv * n + j, t0);
+            }
+            if (tid == 0) {
+                const C<L> t0 = ld_c<L>(b, n, k);
+                st_c<L>(b, n, k, ld_c<L>(b, n, piv));
+                st_c<L>(b, n, piv, t0);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) st_c<L>(A, ap, (size_t)k * n + k, c_inv(ld_c<L>(A, ap, (size_t)k * n + k)));
+        __syncthreads();
+        const C<L> inv = ld_c<L>(A, ap, (size_t)k * n + k);
+        for (int i = k + 1 + tid; i < n; i += HC_TB)
+            st_c<L>(A, ap, (size_t)i * n + k, c_mul(ld_c<L>(A, ap, (size_t)i * n + k), inv));
+        __syncthreads();
+        const int w = n - k;  // columns k+1..n-1 and b
+        const int cnt = (n - k - 1) * w;
+        for (int idx = tid; idx < cnt; idx += HC_TB) {
+            const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+            const C<L> l = ld_c<L>(A, ap, (size_t)i * n + k);
+            if (j < n)
+                st_c<L>(A, ap, (size_t)i * n + j, c_fnma(ld_c<L>(A, ap, (size_t)i * n + j), l, ld_c<L>(A, ap, (size_t)k * n + j)));
+            else
+                st_c<L>(b, n, i, c_fnma(ld_c<L>(b, n, i), l, ld_c<L>(b, n, k)));
+        }
+        __syncthreads();
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        if (tid == 0) st_c<L>(b, n, i, c_mul(ld_c<L>(b, n, i), ld_c<L>(A, ap, (size_t)i * n + i)));
+        __syncthreads();
+        const C<L> zi = ld_c<L>(b, n, i);
+        for (int r = tid; r < i; r += HC_TB)
+            st_c<L>(b, n, r, c_fnma(ld_c<L>(b, n, r), ld_c<L>(A, ap, (size_t)r * n + i), zi));
+        __syncthreads();
+    }
+    *cond = 0.5 * log10(pmax / pmin);
+    return HC_OK;
+}
+
+struct cdv { double re, im; };
+__device__ __forceinline__ cdv cdv_mul(cdv a, cdv b) { return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)}; }
+__device__ __forceinline__ cdv cdv_fnma(cdv acc, cdv a, cdv b)
+{
+    return {fma(-a.re, b.re, fma(a.im, b.im, acc.re)), fma(-a.re, b.im, fma(-a.im, b.re, acc.im))};
+}
+
+// FP64 LU of the leading limbs with partial pivoting (the same pivot rule), block version.
+// B[2][n][n] gets L (unit, below the diagonal), U, and the reciprocals of U's diagonal.
+template <int L>
+__device__ int block_lu64(int n, const double *__restrict__ A, double *__restrict__ B, int32_t *__restrict__ PIV,
+                          BlockShared &sh, double *cond)
+{
+    const int tid = threadIdx.x;
+    const size_t ap = (size_t)n * n;
+    for (int q = tid; q < n * n; q += HC_TB) {
+        double re, im;
+        ld_lead<L>(A, ap, q, re, im);
+        B[q] = re;
+        B[ap + q] = im;
+    }
+    __syncthreads();
+    auto ld = [&](int i, int j) { return cdv{B[(size_t)i * n + j], B[ap + (size_t)i * n + j]}; };
+    auto st = [&](int i, int j, cdv v) { B[(size_t)i * n + j] = v.re; B[ap + (size_t)i * n + j] = v.im; };
+    double pmax = 0.0, pmin = INFINITY;
+    for (int k = 0; k < n; k++) {
+        double bv = -1.0;
+        int bi = 0x7fffffff;
+        for (int i = k + tid; i < n; i += HC_TB) {
+            const cdv a = ld(i, k);
+            const double v = add_(mul_(a.re, a.re), mul_(a.im, a.im));
+            if (v > bv) {
+                bv = v;
+                bi = i;
+            }
+        }
+        block_argmax(bv, bi, sh);
+        if (!(bv > 0.0)) return HC_SINGULAR;
+        pmax = fmax(pmax, bv);
+        pmin = fmin(pmin, bv);
+        const int piv = bi;
+        if (tid == 0) PIV[k] = piv;
+        if (piv != k)
+            for (int j = tid; j < n; j += HC_TB) {
+                const cdv t0 = ld(k, j);
+                st(k, j, ld(piv, j));
+                st(piv, j, t0);
+            }
+        __syncthreads();
+        const cdv a = ld(k, k);
+        const cdv inv = {a.re / bv, -a.im / bv};
+        for (int i = k + 1 + tid; i < n; i += HC_TB) st(i, k, cdv_mul(ld(i, k), inv));
+        __syncthreads();
+        if (tid == 0) st(k, k, inv);
+        const int w = n - k - 1;
+        for (int idx = tid; idx < w * w; idx += HC_TB) {
+            const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+            st(i, j, cdv_fnma(ld(i, j), ld(i, k), ld(k, j)));
+        }
+        __syncthreads();
+    }
+    *cond = 0.5 * log10(pmax / pmin);
+    return HC_OK;
+}
+
+// solve with the FP64 LU: RV[2][n] in place
+__device__ void block_lu64_solve(int n, const double *__restrict__ B, const int32_t *__restrict__ PIV,
+                                 double *__restrict__ RV)
+{
+    const int tid = threadIdx.x;
+    const size_t ap = (size_t)n * n;
+    if (tid == 0)
+        for (int k = 0; k < n; k++) {
+            const int p = PIV[k];
+            if (p != k) {
+                double t0 = RV[k], t1 = RV[n + k];
+                RV[k] = RV[p];
+                RV[n + k] = RV[n + p];
+                RV[p] = t0;
+                RV[n + p] = t1;
+            }
+        }
+    __syncthreads();
+    for (int k = 0; k < n - 1; k++) {
+        const cdv rk = {RV[k], RV[n + k]};
+        for (int i = k + 1 + tid; i < n; i += HC_TB) {
+            const cdv v = cdv_fnma(cdv{RV[i], RV[n + i]}, cdv{B[(size_t)i * n + k], B[ap + (size_t)i * n + k]}, rk);
+            RV[i] = v.re;
+            RV[n + i] = v.im;
+        }
+        __syncthreads();
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        if (tid == 0) {
+            const cdv v = cdv_mul(cdv{RV[i], RV[n + i]}, cdv{B[(size_t)i * n + i], B[ap + (size_t)i * n + i]});
+            RV[i] = v.re;
+            RV[n + i] = v.im;
+        }
+        __syncthreads();
+        const cdv zi = {RV[i], RV[n + i]};
+        for (int r = tid; r < i; r += HC_TB) {
+            const cdv v = cdv_fnma(cdv{RV[r], RV[n + r]}, cdv{B[(size_t)r * n + i], B[ap + (size_t)r * n + i]}, zi);
+            RV[r] = v.re;
+            RV[n + r] = v.im;
+        }
+        __syncthreads();
+    }
+}
+
+struct NewtonOut {
+    double res, dzn, zn, cond;
+    int status, sweeps;
+};
+
+//
+// One Newton iteration of Alg. 4.1 at z (in place): evaluate h and J, the residual of the
+// incoming z (max_i |h_i| of the leading limbs), solve J dz = -h, z += dz (all or nothing
+// on non-finite values).  Same readings as hc_newton_step.
+//
+template <int L>
+__device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, double t, int lu_mode, int max_refine,
+                                  const Slot<L> &w, BlockShared &sh)
+{
+    const int n = S.n, tid = threadIdx.x;
+    NewtonOut o{0.0, 0.0, 0.0, 0.0, HC_OK, 0};
+    block_eval<L>(S, z, t, w);
+    double r2 = 0.0;
+    int fin = 1;
+    for (int i = tid; i < n; i += HC_TB) {
+        double re, im;
+        ld_lead<L>(w.H, n, i, re, im);
+        const double v = add_(mul_(re, re), mul_(im, im));
+        if (!isfinite(v)) fin = 0;
+        r2 = fmax(r2, v);
+    }
+    fin = block_and(fin, sh);
+    o.res = sqrt(block_max(r2, sh));
+    if (!fin) {
+        o.status = HC_NONFINITE;
+        return o;
+    }
+    const double *D;  // the update, [2][L][n]
+    bool subtract;
+    if (lu_mode == HC_LU_NATIVE) {
+        o.status = block_ge<L>(n, w.JH, w.H, sh, &o.cond);
+        if (o.status != HC_OK) return o;
+        D = w.H;
+        subtract = true;
+    } else {
+        o.status = block_lu64<L>(n, w.JH, w.B, w.PIV, sh, &o.cond);
+        if (o.status != HC_OK) return o;
+        for (int i = tid; i < n; i += HC_TB) {
+            double re, im;
+            ld_lead<L>(w.H, n, i, re, im);
+            w.RV[i] = -re;
+            w.RV[n + i] = -im;
+        }
+        __syncthreads();
+        block_lu64_solve(n, w.B, w.PIV, w.RV);
+        double xn = 0.0;
+        for (int i = tid; i < n; i += HC_TB) {
+            st_c<L>(w.DZ, n, i, c_from<L>(w.RV[i], w.RV[n + i]));
+            double re, im;
+            ld_lead<L>(z, n, i, re, im);
+            xn = fmax(xn, sqrt(add_(mul_(re, re), mul_(im, im))));
+        }
+        xn = block_max(xn, sh);
+        const double tol = ldexp(1.0, -53 * L);
+        double prev = INFINITY;
+        for (int it = 1; it <= max_refine; it++) {
+            for (int i = tid; i < n; i += HC_TB) {
+                C<L> acc = ld_c<L>(w.H, n, i);
+                acc.re = r_neg(acc.re);
+                acc.im = r_neg(acc.im);
+                for (int j = 0; j < n; j++)
+                    acc = c_fnma(acc, ld_c<L>(w.JH, (size_t)n * n, (size_t)i * n + j), ld_c<L>(w.DZ, n, j));
+                w.RV[i] = acc.re.v[0];
+                w.RV[n + i] = acc.im.v[0];
+            }
+            __syncthreads();
+            block_lu64_solve(n, w.B, w.PIV, w.RV);
+            double dn = 0.0, zz = 0.0;
+            for (int i = tid; i < n; i += HC_TB) {
+                const double dr = w.RV[i], di = w.RV[n + i];
+                const C<L> v = c_add(ld_c<L>(w.DZ, n, i), c_from<L>(dr, di));
+                st_c<L>(w.DZ, n, i, v);
+                dn = fmax(dn, sqrt(add_(mul_(dr, dr), mul_(di, di))));
+                zz = fmax(zz, sqrt(c_abs2_lead(v)));
+            }
+            dn = block_max(dn, sh);
+            zz = block_max(zz, sh);
+            o.sweeps = it;
+            if (dn <= tol * fmax(xn, zz) || dn >= prev) break;
+            prev = dn;
+        }
+        D = w.DZ;
+        subtract = false;
+    }
+    // update, all or nothing
+    int ok = 1;
+    double dzn = 0.0, zn = 0.0;
+    for (int i = tid; i < n; i += HC_TB) {
+        const C<L> d = ld_c<L>(D, n, i);
+        const C<L> v = subtract ? c_sub(ld_c<L>(z, n, i), d) : c_add(ld_c<L>(z, n, i), d);
+        if (!c_finite_lead(v)) ok = 0;
+        dzn = fmax(dzn, sqrt(c_abs2_lead(d)));
+        zn = fmax(zn, sqrt(c_abs2_lead(v)));
+    }
+    ok = block_and(ok, sh);
+    o.dzn = block_max(dzn, sh);
+    o.zn = block_max(zn, sh);
+    if (!ok) {
+        o.status = HC_NONFINITE;
+        return o;
+    }
+    for (int i = tid; i < n; i += HC_TB) {
+        const C<L> d = ld_c<L>(D, n, i);
+        st_c<L>(z, n, i, subtract ? c_sub(ld_c<L>(z, n, i), d) : c_add(ld_c<L>(z, n, i), d));
+    }
+    __syncthreads();
+    return o;
+}
+
+}  // namespace hc

@@ -29,6 +29,32 @@ _lock = threading.Lock()
 _lib = None
 
 
+class TrackOpts(ct.Structure):
+    """hc_track_opts (include/hc.h)."""
+    _fields_ = [("lambda0", ct.c_double), ("lambda_min", ct.c_double),
+                ("lambda_max", ct.c_double), ("grow", ct.c_double), ("shrink", ct.c_double),
+                ("eps", ct.c_double), ("eps_x", ct.c_double), ("eps_end", ct.c_double),
+                ("eps_end_x", ct.c_double), ("div_bound", ct.c_double),
+                ("max_it", ct.c_int32), ("end_it", ct.c_int32), ("grow_after", ct.c_int32),
+                ("max_steps", ct.c_int32), ("predictor", ct.c_int32), ("lu_mode", ct.c_int32),
+                ("max_refine", ct.c_int32), ("mode", ct.c_int32), ("graph_steps", ct.c_int32),
+                ("reserved", ct.c_int32)]
+
+
+class PathStats(ct.Structure):
+    """hc_path_stats (include/hc.h)."""
+    _fields_ = [("n_succ", ct.c_int64), ("n_corr", ct.c_int64), ("newton_its", ct.c_int64),
+                ("min_step", ct.c_double), ("avg_step", ct.c_double), ("t_end", ct.c_double),
+                ("res_end", ct.c_double), ("status", ct.c_int32), ("end_its", ct.c_int32)]
+
+
+STEP_RECORD_DTYPE = np.dtype([("t", "f8"), ("lam", "f8"), ("res_first", "f8"), ("res_last", "f8"),
+                              ("pc_dist", "f8"), ("cond_log10", "f8"), ("iters", "i4"),
+                              ("accepted", "i4")])
+HC_PRED_SECANT, HC_PRED_QUADRATIC = 0, 1
+HC_TRACK_PERSISTENT, HC_TRACK_GRAPH = 0, 1
+
+
 class HCError(RuntimeError):
     def __init__(self, fn: str, code: int, msg: str):
         super().__init__(f"{fn} failed with code {code}: {msg}")
@@ -70,6 +96,11 @@ def load(build_if_missing: bool = True):
         L.hc_probe_fp64_peak.restype = i
         L.hc_set_tiles.argtypes = [i, i]
         L.hc_set_tiles.restype = i
+        L.hc_track_opts_default.argtypes = [ct.POINTER(TrackOpts)]
+        L.hc_track_opts_default.restype = None
+        L.hc_track_path.argtypes = [ct.POINTER(vp), i, vp, vp, ct.POINTER(TrackOpts),
+                                    ct.POINTER(PathStats), vp, i, vp]
+        L.hc_track_path.restype = i
         L.hc_eval_jac_noalloc.argtypes = [vp, i, d, vp, vp, vp, vp]
         L.hc_eval_jac_noalloc.restype = i
         L.hc_prof_enable.argtypes = [i]
@@ -176,6 +207,41 @@ def hc_newton_step(sys: System, npts: int, t: float, x, lu_mode: int, max_refine
     _check("hc_newton_step", load().hc_newton_step(
         sys.handle, int(npts), float(t), _ptr(x), int(lu_mode), int(max_refine), _ptr(res_norm),
         _ptr(status), _ptr(sweeps), _stream(stream)))
+
+
+def hc_track_opts_default(**over) -> TrackOpts:
+    o = TrackOpts()
+    load().hc_track_opts_default(ct.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def hc_track_path(systems, x0, x1, opts: TrackOpts, log=None, log_cap: int = 0,
+                  stream=None) -> list[dict]:
+    """Track one path per system (a system may repeat).  x0/x1: device buffers packed
+    path after path ([2][L][n_p] each); log: device buffer of hc_step_record."""
+    handles = (ct.c_void_p * len(systems))(*[s.handle for s in systems])
+    stats = (PathStats * len(systems))()
+    _check("hc_track_path", load().hc_track_path(handles, len(systems), _ptr(x0), _ptr(x1),
+                                                 ct.byref(opts), stats, _ptr(log), int(log_cap),
+                                                 _stream(stream)))
+    keys = [f[0] for f in PathStats._fields_]
+    return [{k: getattr(st, k) for k in keys} for st in stats]
+
+
+def pack_paths(points: list[np.ndarray]) -> np.ndarray:
+    """Start points (each limbs [n_p][2][L]) -> the packed layout of hc_track_path."""
+    return np.concatenate([np.ascontiguousarray(np.transpose(p, (1, 2, 0))).ravel() for p in points])
+
+
+def unpack_paths(buf: np.ndarray, dims: list[int], L: int) -> list[np.ndarray]:
+    """Inverse of pack_paths: list of limbs [n_p][2][L]."""
+    out, o = [], 0
+    for n in dims:
+        out.append(np.ascontiguousarray(np.transpose(buf[o:o + 2 * L * n].reshape(2, L, n), (2, 0, 1))))
+        o += 2 * L * n
+    return out
 
 
 def hc_probe_fp64_peak() -> float:

@@ -113,6 +113,39 @@ def unit_complex(rng: np.random.Generator) -> complex:
     return complex(np.cos(th), np.sin(th))
 
 
+def regular_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
+                   lead: int) -> System:
+    """A random system (as random_system) plus, in polynomial i, the monomial x_i^D with
+    coefficient 1, D = max(lead, 1 + the largest total degree of the other monomials).
+    Its leading forms then vanish together only at 0, so no path of the total-degree
+    homotopy goes to infinity: test systems whose paths should end at roots.  Each
+    polynomial also gets a constant term, so that x = 0 (a singular root of a system
+    without constants) is not a root."""
+    s = random_system(rng, n, mons_per_poly, k, exps, const_term=True)
+    top = 0
+    for m in range(s.nmon):
+        top = max(top, int(s.var_exp[s.var_ptr[m]:s.var_ptr[m + 1]].sum()))
+    lead = max(lead, top + 1)
+    mon_ptr = [0]
+    var_ptr = [0]
+    idx, ex, coef = [], [], []
+    for i in range(n):
+        for m in range(s.mon_ptr[i], s.mon_ptr[i + 1]):
+            q0, q1 = s.var_ptr[m], s.var_ptr[m + 1]
+            idx.extend(s.var_idx[q0:q1])
+            ex.extend(s.var_exp[q0:q1])
+            var_ptr.append(var_ptr[-1] + (q1 - q0))
+            coef.append(s.coef[m])
+        idx.append(i)
+        ex.append(lead)
+        var_ptr.append(var_ptr[-1] + 1)
+        coef.append(1.0 + 0j)
+        mon_ptr.append(len(coef))
+    return System(n=n, npoly=n, mon_ptr=np.array(mon_ptr, np.int32),
+                  var_ptr=np.array(var_ptr, np.int32), var_idx=np.array(idx, np.int32),
+                  var_exp=np.array(ex, np.int32), coef=np.array(coef))
+
+
 # ---------------------------------------------------------------------------------------
 # The workloads.  Each returns plain data; sizes can be reduced for tests.
 # ---------------------------------------------------------------------------------------

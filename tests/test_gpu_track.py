@@ -1,0 +1,168 @@
+"""hc_track_path against the oracle tracker (Alg. 3.1 + Alg. 4.1, same readings, same
+options): per path the status, the accepted/total corrector stages, and the end point
+within the tolerance of the precision; batched (one launch for all paths) and one path
+per launch agree bit for bit; the persistent kernel and the graph-stepped mode agree
+bit for bit."""
+import numpy as np
+import pytest
+
+from helpers import TOL, digits, rel_err_per_point
+from gpu_util import torch_cuda
+import oracle
+from paper_1109_0545_gb300 import hc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_opts(o: "hc.TrackOpts"):
+    return oracle.TrackOpts(lambda0=o.lambda0, lambda_min=o.lambda_min, lambda_max=o.lambda_max,
+                            grow=o.grow, shrink=o.shrink, eps=o.eps, eps_x=o.eps_x,
+                            eps_end=o.eps_end, eps_end_x=o.eps_end_x, div_bound=o.div_bound,
+                            max_it=o.max_it, end_it=o.end_it, grow_after=o.grow_after,
+                            max_steps=o.max_steps, predictor=o.predictor, lu_mode=o.lu_mode,
+                            max_refine=o.max_refine)
+
+
+def gpu_track(torch, systems, gammas, L, opts, starts=None, log_cap=0):
+    handles = [hc.system_from(s, L, g) for s, g in zip(systems, gammas)]
+    if starts is None:
+        starts = [synth.limbs(np.ones(s.n), L) for s in systems]
+    x0 = torch.from_numpy(hc.pack_paths(starts)).cuda()
+    x1 = torch.zeros_like(x0)
+    log = None
+    if log_cap:
+        log = torch.zeros(len(systems) * log_cap * hc.STEP_RECORD_DTYPE.itemsize, dtype=torch.uint8,
+                          device="cuda")
+    stats = hc.hc_track_path(handles, x0, x1, opts, log, log_cap)
+    torch.cuda.synchronize()
+    ends = hc.unpack_paths(x1.cpu().numpy(), [s.n for s in systems], L)
+    recs = None
+    if log_cap:
+        recs = log.cpu().numpy().view(hc.STEP_RECORD_DTYPE).reshape(len(systems), log_cap)
+    for h in handles:
+        h.free()
+    return stats, ends, recs
+
+
+def regular_family(seed, count, n, L_lead=3):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        s = synth.regular_system(rng, n, 4, (1, min(2, n)), (1, 2), lead=L_lead)
+        out.append((s, synth.unit_complex(rng)))
+    return out
+
+
+def compare_with_oracle(systems, gammas, L, opts, stats, ends, strict_counts=True):
+    oo = oracle_opts(opts)
+    n_ok = 0
+    for s, g, st, x in zip(systems, gammas, stats, ends):
+        r = oracle.track(s.as_dict(), s.coef_limbs(L), synth.limbs(np.ones(s.n), L),
+                         np.array([g.real, g.imag]), oo)
+        assert st["status"] == r.status, (st, oracle.STATUS[r.status])
+        if strict_counts:
+            assert (st["n_succ"], st["n_corr"]) == (r.n_succ, r.n_corr)
+        if r.status == 0:
+            e = rel_err_per_point(x[None], r.x[None])
+            assert e[0] <= TOL[L], (e, digits(e))
+            n_ok += 1
+    return n_ok
+
+
+@pytest.mark.parametrize("lu_mode", [hc.HC_LU_NATIVE, hc.HC_LU_FP64_REFINE])
+def test_regular_systems_dd_match_oracle(lu_mode):
+    torch = torch_cuda()
+    fam = regular_family(400, 8, 3)
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    opts = hc.hc_track_opts_default(lu_mode=lu_mode)
+    stats, ends, _ = gpu_track(torch, systems, gammas, 2, opts)
+    n_ok = compare_with_oracle(systems, gammas, 2, opts, stats, ends)
+    print(f"lu_mode={lu_mode}: {n_ok} of {len(systems)} paths end at a root; statuses "
+          f"{[hc.STATUS_NAMES[s['status']] for s in stats]}")
+    assert n_ok == len(systems)
+
+
+@pytest.mark.parametrize("L", [1, 4])
+def test_regular_systems_double_and_qd(L):
+    torch = torch_cuda()
+    fam = regular_family(410, 4, 2)
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    opts = hc.hc_track_opts_default()
+    if L == 1:
+        opts.eps, opts.eps_end, opts.eps_end_x = 1e-12, 1e-12, 1e-12
+    else:
+        opts.eps, opts.eps_end, opts.eps_end_x = 1e-58, 1e-58, 1e-58
+    stats, ends, _ = gpu_track(torch, systems, gammas, L, opts)
+    n_ok = compare_with_oracle(systems, gammas, L, opts, stats, ends)
+    assert n_ok == len(systems)
+
+
+def test_quadratic_predictor_matches_oracle():
+    torch = torch_cuda()
+    fam = regular_family(420, 6, 3)
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    opts = hc.hc_track_opts_default(predictor=hc.HC_PRED_QUADRATIC)
+    stats, ends, _ = gpu_track(torch, systems, gammas, 2, opts)
+    assert compare_with_oracle(systems, gammas, 2, opts, stats, ends) == len(systems)
+
+
+def test_single_path_workload_matches_oracle():
+    """n = 8, 12 monomials + constant, k = 3: the path from (1..1) goes to infinity;
+    both trackers take the same stages and stop the same way."""
+    torch = torch_cuda()
+    s, g = synth.single_path_dd(1)
+    opts = hc.hc_track_opts_default()
+    stats, ends, _ = gpu_track(torch, [s], [g], 2, opts)
+    r = oracle.track(s.as_dict(), s.coef_limbs(2), synth.limbs(np.ones(8), 2),
+                     np.array([g.real, g.imag]), oracle_opts(opts))
+    st = stats[0]
+    print("gpu", st, "oracle", oracle.STATUS[r.status], r.n_succ, r.n_corr, r.t_end)
+    assert st["status"] == r.status
+    assert (st["n_succ"], st["n_corr"]) == (r.n_succ, r.n_corr)
+    assert st["t_end"] == r.t_end
+
+
+def test_graph_mode_and_one_path_per_launch_agree_bitwise():
+    torch = torch_cuda()
+    fam = regular_family(430, 5, 3)
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    opts = hc.hc_track_opts_default()
+    a_stats, a_ends, a_log = gpu_track(torch, systems, gammas, 2, opts, log_cap=400)
+    g_opts = hc.hc_track_opts_default(mode=hc.HC_TRACK_GRAPH, graph_steps=8)
+    b_stats, b_ends, b_log = gpu_track(torch, systems, gammas, 2, g_opts, log_cap=400)
+    assert a_stats == b_stats
+    for x, y in zip(a_ends, b_ends):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a_log, b_log)
+    for p in range(len(systems)):
+        st, ends, _ = gpu_track(torch, [systems[p]], [gammas[p]], 2, opts)
+        assert st[0] == a_stats[p] and np.array_equal(ends[0], a_ends[p])
+    # the log holds one record per corrector stage; accepted steps add up to t_end
+    for p, st in enumerate(a_stats):
+        recs = a_log[p, :st["n_corr"]]
+        assert recs["accepted"].sum() == st["n_succ"]
+        assert abs(recs["lam"][recs["accepted"] == 1].sum() - st["t_end"]) < 1e-12
+
+
+def test_uneven_family_end_points_are_roots():
+    """Systems of the batched uneven-path family (n in 10..64, 20..200 monomials per
+    polynomial): too large for the oracle to track, so every path that the GPU reports
+    OK is checked at its end point -- the oracle's residual there is at DD rounding level
+    and its Newton step from there moves the point by less than 1e-25 (relative)."""
+    torch = torch_cuda()
+    fam = [synth.uneven_path_system(3, j) for j in range(12)]
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    opts = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC)
+    stats, ends, _ = gpu_track(torch, systems, gammas, 2, opts)
+    print([(s.n, hc.STATUS_NAMES[st["status"]], st["n_corr"]) for s, st in zip(systems, stats)])
+    for s, g, st, x in zip(systems, gammas, stats, ends):
+        assert st["status"] in range(7)
+        if st["status"] != 0:
+            continue
+        ga = np.array([g.real, g.imag])
+        f, _, _ = oracle.evaluate(s.as_dict(), s.coef_limbs(2), x[None], -1.0, ga, jac=False)
+        scale = np.abs(s.coef).max() * max(1.0, np.abs(x[:, :, 0]).max()) ** int(s.var_exp.max() * 8)
+        assert np.abs(f[..., 0]).max() <= 1e-26 * scale
+        xn, _, stn, _ = oracle.newton_step(s.as_dict(), s.coef_limbs(2), x[None], -1.0, ga, 0)
+        assert stn[0] == 0
+        assert rel_err_per_point(xn, x[None])[0] < 1e-25
