@@ -180,6 +180,71 @@ def captured_traffic(npts: int):
     return per_pt * npts
 
 
+def tracker_bench(torch, hc, synth, npaths=128, plain_sample=2):
+    """Path steps/s of the batched tracker (all paths in one persistent kernel, FP64 LU
+    + DD refinement) against the plain GPU tracker (all-DD elimination, one path per
+    launch), on the uneven-path family (n 10..64, 20..200 monomials per polynomial,
+    k 2..8, exponents 1..3, seed 3) and on its regular variant (a pure power and a
+    constant per polynomial, so that paths end at regular roots); plus the secant
+    against the quadratic predictor (Sec. 5) on the regular variant."""
+    import numpy as np
+    out = {}
+
+    def run(systems, gammas, opts):
+        handles = [hc.system_from(s, 2, g) for s, g in zip(systems, gammas)]
+        x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 2) for s in systems])).cuda()
+        x1 = torch.zeros_like(x0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = hc.hc_track_path(handles, x0, x1, opts)
+        dt = time.perf_counter() - t0
+        for h in handles:
+            h.free()
+        return stats, dt
+
+    fams = {"uneven": [synth.uneven_path_system(3, j) for j in range(npaths)]}
+    rng = np.random.default_rng(33)
+    reg = []
+    for j in range(npaths):
+        n = int(rng.integers(10, 65))
+        reg.append((synth.regular_system(rng, n, (20, 200), (2, 8), (1, 3), lead=1),
+                    synth.unit_complex(rng)))
+    fams["uneven_regular"] = reg
+    for name, fam in fams.items():
+        systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+        ours = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE)
+        st, dt = run(systems, gammas, ours)
+        steps = sum(x["n_corr"] for x in st)
+        plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE)
+        p_steps, p_dt = 0, 0.0
+        for j in range(plain_sample):
+            pst, pdt = run(systems[j:j + 1], gammas[j:j + 1], plain)
+            p_steps += pst[0]["n_corr"]
+            p_dt += pdt
+        ok = [x for x in st if x["status"] == hc.HC_OK]
+        out[name] = {"paths": npaths, "batched_path_steps_per_s": steps / dt,
+                     "batched_paths_per_s": npaths / dt,
+                     "plain_path_steps_per_s": p_steps / p_dt,
+                     "plain_paths_per_s": plain_sample / p_dt,
+                     "plain_sample_paths": plain_sample,
+                     "speedup_steps": (steps / dt) / (p_steps / p_dt),
+                     "ok_paths": len(ok),
+                     "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
+    systems, gammas = [f[0] for f in reg], [f[1] for f in reg]
+    cmp = {}
+    for pred, nm in ((hc.HC_PRED_SECANT, "secant"), (hc.HC_PRED_QUADRATIC, "quadratic")):
+        st, dt = run(systems, gammas, hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE,
+                                                               predictor=pred))
+        ok = [x for x in st if x["status"] == hc.HC_OK]
+        cmp[nm] = {"mean_succ": float(np.mean([x["n_succ"] for x in ok])) if ok else None,
+                   "mean_corr": float(np.mean([x["n_corr"] for x in ok])) if ok else None,
+                   "mean_avg_step": float(np.mean([x["avg_step"] for x in ok])) if ok else None,
+                   "min_step": float(min(x["min_step"] for x in ok)) if ok else None,
+                   "ok_paths": len(ok), "seconds": dt}
+    out["predictors_regular"] = cmp
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -215,6 +280,15 @@ def run_gpu(args):
     def step(lu=hc.HC_LU_FP64_REFINE):
         hc.hc_newton_step(sysh, npts, T_HOM, x, lu, MAX_REFINE, res, st, sw, stream)
 
+    # tile shape of the evaluation kernel, tuned on this workload (outside the timing)
+    from paper_1109_0545_gb300 import autotune
+    fbuf = torch.empty((2, L, s.npoly, npts), dtype=torch.float64, device="cuda")
+    jbuf = torch.empty((2, L, s.npoly, s.n, npts), dtype=torch.float64, device="cuda")
+    tiles = autotune.tune_eval(sysh, x0, fbuf, jbuf, npts, T_HOM, reps=1, use_cache=False,
+                               candidates=[(0, 0), (1, 4), (2, 4), (4, 4), (1, 6), (2, 6),
+                                           (4, 6), (8, 6), (1, 8), (2, 8)])
+    del fbuf, jbuf
+    tiles.pop("tried", None)
     for _ in range(max(args.warmup, 0)):
         x.copy_(x0)
         step()
@@ -289,7 +363,8 @@ def run_gpu(args):
         J = torch.empty((2, L, s.npoly, s.n, npts), dtype=torch.float64, device="cuda")
         ms_eval = timed(lambda: hc.hc_eval_jac(sysh, npts, T_HOM, x, f, J, stream))
         del f, J
-        extras = {"newton_native_dd_lu_points_per_s": npts / (ms_native * 1e-3),
+        extras = {"tracker": tracker_bench(torch, hc, synth),
+                  "newton_native_dd_lu_points_per_s": npts / (ms_native * 1e-3),
                   "eval_jac_points_per_s": npts / (ms_eval * 1e-3),
                   "refine_sweeps_hist": np.bincount(sweeps, minlength=MAX_REFINE + 1).tolist(),
                   "status_ok_frac": float(np.mean(status == hc.HC_OK))}
@@ -331,7 +406,8 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "npts": npts, "n": s.n, "monomials": s.nmon,
                        "precision": "complex double-double", "lu": "FP64 LU + DD refinement",
                        "max_refine": MAX_REFINE, "t": T_HOM, "parallelism": f"dp{world}",
-                       "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)"},
+                       "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)",
+                       "eval_tiles": tiles},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clk, "wall_s": t_wall,
             "extras": extras,

@@ -123,3 +123,62 @@ def test_eval_throughput_workload_full_size_sampled(L):
     print(f"L={L} full size: f {digits(ef):.1f} digits, J {digits(eJ):.1f} digits")
     assert np.all(ef <= TOL[L]) and np.all(eJ <= TOL[L])
     sysh.free()
+
+
+def _rows_subsystem(s, rows):
+    """The polynomials `rows` of s as a system of its own (same n)."""
+    mon_ptr, var_ptr, idx, ex, coef = [0], [0], [], [], []
+    for i in rows:
+        for m in range(s.mon_ptr[i], s.mon_ptr[i + 1]):
+            q0, q1 = s.var_ptr[m], s.var_ptr[m + 1]
+            idx.extend(s.var_idx[q0:q1])
+            ex.extend(s.var_exp[q0:q1])
+            var_ptr.append(var_ptr[-1] + q1 - q0)
+            coef.append(s.coef[m])
+        mon_ptr.append(len(coef))
+    return synth.System(n=s.n, npoly=len(rows), mon_ptr=np.array(mon_ptr, np.int32),
+                        var_ptr=np.array(var_ptr, np.int32), var_idx=np.array(idx, np.int32),
+                        var_exp=np.array(ex, np.int32), coef=np.array(coef))
+
+
+def test_large_qd_workload_sampled_rows():
+    """n = 96, 96 x 1024 monomials, k = 12, exponents 1..5, complex QD: the full system
+    on the GPU at 40 points; the oracle evaluates rows 0, 50 and 95 at 2 points."""
+    torch = torch_cuda()
+    s, gamma = synth.large_path_qd(4)
+    rng = np.random.default_rng(240)
+    pts = limbs_of(synth.torus_points(rng, 40, s.n), 4)
+    f, J = gpu_eval(torch, s, gamma, 4, pts, -1.0)
+    rows = [0, 50, 95]
+    sub = _rows_subsystem(s, rows)
+    sample = [0, 39]
+    fo, Jo = oracle_eval(sub, gamma, 4, pts[sample], -1.0)
+    ef = rel_err_per_point(f[sample][:, rows], fo)
+    eJ = rel_err_per_point(J[sample][:, rows], Jo)
+    print(f"large QD: f {digits(ef):.1f} digits, J {digits(eJ):.1f} digits")
+    assert np.all(ef <= TOL[4]) and np.all(eJ <= TOL[4])
+
+
+def test_autotuned_tiles_give_identical_results():
+    """Every tile shape computes the same bits (a point's arithmetic does not depend on
+    how the work is cut), and the tuner returns one of the candidates."""
+    torch = torch_cuda()
+    from paper_1109_0545_gb300 import autotune
+    s, pts, gamma = synth.eval_throughput(2, npts=2000)
+    sysh = hc.system_from(s, 2, gamma)
+    x = torch.from_numpy(hc.to_soa(pts, 2)).cuda()
+    f = torch.zeros((2, 2, 32, 2000), dtype=torch.float64, device="cuda")
+    J = torch.zeros((2, 2, 32, 32, 2000), dtype=torch.float64, device="cuda")
+    ref = None
+    for r, b in [(0, 0), (1, 2), (3, 3), (8, 6), (32, 1)]:
+        hc.hc_set_tiles(r, b)
+        hc.hc_eval_jac(sysh, 2000, 0.3, x, f, J)
+        torch.cuda.synchronize()
+        got = (f.cpu().numpy().copy(), J.cpu().numpy().copy())
+        if ref is None:
+            ref = got
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    best = autotune.tune_eval(sysh, x, f, J, 2000, 0.3, reps=1, use_cache=False)
+    assert (best["rows_per_task"], best["blocks_per_sm"]) in [(r, b) for r in autotune.ROWS for b in autotune.BLOCKS]
+    hc.hc_set_tiles(0, 0)
+    sysh.free()
