@@ -163,6 +163,9 @@ typedef struct {
     int32_t mode;       /* HC_TRACK_PERSISTENT or HC_TRACK_GRAPH */
     int32_t graph_steps;/* launches per graph in HC_TRACK_GRAPH, 16 */
     int32_t reserved;
+    const float *proposer;   /* device, HC_MLP_NPARAM weights of the learned step
+                                proposer, or NULL for the plain controller */
+    double proposer_margin;  /* the proposal is lambda_last * 2^(m - margin), 0.5 */
 } hc_track_opts;
 
 /* Per-path result (the statistics of Tables 2-3). */
@@ -215,6 +218,41 @@ void hc_track_opts_default(hc_track_opts *opts);
 int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x1,
                   const hc_track_opts *opts, hc_path_stats *stats, hc_step_record *log,
                   int log_cap, void *stream);
+
+/*
+ * The learned step-size proposer (not in the paper; the plain controller of Alg. 3.1
+ * stays the fallback and the corrector still judges every step): a 12 -> 64 -> 64 -> 1
+ * perceptron with GELU, bfloat16 operands, float32 accumulation and float32 master
+ * weights.  Parameters, HC_MLP_NPARAM floats: W1 (64x12, row-major) | b1 (64) |
+ * W2 (64x64) | b2 (64) | W3 (64) | b3 (1).  Its output m estimates log2 of the largest
+ * next step, relative to the last attempted one, that the corrector would accept.
+ * Features (HC_MLP_IN floats per record, scaled to order one): t;
+ * log2(lambda/lambda0)/8 of the last three attempted steps; their Newton iteration
+ * counts/4; log10 of their last residuals, clipped to [-40, 5], /10; the same for the
+ * last predictor-corrector distance (-4 after a rejection); the last condition estimate
+ * (hc_step_record.cond_log10)/4.  Missing history: steps lambda0, 0 iterations,
+ * residual and distance -4, condition 0.
+ * Training loss per logged stage with attempted log2 step ratio r and outcome a:
+ * z = m - r, softplus(-kappa z) if accepted else softplus(kappa z), averaged.
+ * All pointers are device pointers; the calls are asynchronous on the stream.
+ */
+#define HC_MLP_IN 12
+#define HC_MLP_NPARAM 5057
+
+/* grad[HC_MLP_NPARAM] = gradient of the mean loss over nrec records (feat[nrec][12],
+ * target[nrec] = r, accepted[nrec]); *loss = the mean loss (loss may be NULL).  The
+ * summation order is fixed: results are reproducible bit for bit.  Errors: HC_EINVAL,
+ * HC_ENOMEM, HC_ECUDA. */
+int hc_mlp_grad(const float *params, int nrec, const float *feat, const float *target,
+                const int32_t *accepted, float kappa, float *grad, float *loss, void *stream);
+
+/* One AdamW step (decoupled weight decay) of the float32 master weights; m1, m2 are the
+ * moment buffers (zero before step 1), step counts from 1.  Errors: HC_EINVAL, HC_ECUDA. */
+int hc_mlp_adamw(float *params, float *m1, float *m2, const float *grad, int step, float lr,
+                 float beta1, float beta2, float eps, float wd, void *stream);
+
+/* out[nrec] = m for each feature record.  Errors: HC_EINVAL, HC_ECUDA. */
+int hc_mlp_forward(const float *params, int nrec, const float *feat, float *out, void *stream);
 
 /* Message describing the last failure on the calling host thread ("" if none). */
 const char *hc_last_error(void);

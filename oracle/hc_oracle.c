@@ -1138,6 +1138,108 @@ int or_track(int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr,
     return 0;
 }
 
+/*
+ * Replay: follow a given sequence of accepted parameter values t_1 < t_2 < ... (as a
+ * tracker with any step-size controller produced them) with the predictor and the
+ * corrector of or_track, and then its end game.  Every stage must converge: the oracle
+ * judges each accepted step.  *fail_at gets the index of the first stage the corrector
+ * rejects (status NOCONV), or -1.
+ */
+int or_track_replay(int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr,
+                    const int32_t *var_idx, const int32_t *var_exp, const double *coef,
+                    const double *gamma, const double *x0, const or_opts *o, const double *tseq,
+                    int nseq, double *x1, int32_t *fail_at, or_stats *st)
+{
+    if (!valid_L(L)) return -1;
+    if (or_validate(n, n, mon_ptr, var_ptr, var_idx, var_exp) != 0) return -2;
+    sysdesc s = {n, n, mon_ptr, var_ptr, var_idx, var_exp, coef};
+    int32_t *deg = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    or_degrees(n, mon_ptr, var_ptr, var_exp, deg);
+    C gam = c_from(gamma[0], gamma[1]);
+    size_t nc = (size_t)n;
+    C *z = (C *)malloc(sizeof(C) * nc), *zp = (C *)malloc(sizeof(C) * nc);
+    C *zpp = (C *)malloc(sizeof(C) * nc), *zh = (C *)malloc(sizeof(C) * nc);
+    C *fv = (C *)malloc(sizeof(C) * nc), *Jv = (C *)malloc(sizeof(C) * nc * nc);
+    C *M = (C *)malloc(sizeof(C) * nc * (nc + 1)), *dz = (C *)malloc(sizeof(C) * nc);
+    for (int j = 0; j < n; j++) z[j] = c_load(L, x0 + (size_t)j * 2 * L);
+    double t = 0.0, tp = 0.0, tpp = 0.0;
+    int nhist = 1, status = OR_OK;
+    *fail_at = -1;
+    int64_t nits = 0;
+    for (int k = 0; k < nseq; k++) {
+        double t1 = tseq[k];
+        double h = t1 - t;
+        if (o->predictor == 1 && nhist >= 3) {
+            double w0 = ((t1 - tp) * (t1 - t)) / ((tpp - tp) * (tpp - t));
+            double w1 = ((t1 - tpp) * (t1 - t)) / ((tp - tpp) * (tp - t));
+            double w2 = ((t1 - tpp) * (t1 - tp)) / ((t - tpp) * (t - tp));
+            for (int j = 0; j < n; j++) {
+                C a = c_mul_r(L, zpp[j], r_from_d(w0));
+                C b = c_mul_r(L, zp[j], r_from_d(w1));
+                C c = c_mul_r(L, z[j], r_from_d(w2));
+                zh[j] = c_add(L, c_add(L, a, b), c);
+            }
+        } else if (nhist >= 2) {
+            double r = h / (t - tp);
+            for (int j = 0; j < n; j++)
+                zh[j] = c_add(L, z[j], c_mul_r(L, c_sub(L, z[j], zp[j]), r_from_d(r)));
+        } else {
+            memcpy(zh, z, sizeof(C) * nc);
+        }
+        double res = 1.0, dzn = 0.0, zn = 0.0;
+        int it = 0, nst = OR_OK, conv = 0;
+        while (!conv && it < o->max_it) {
+            int sw;
+            nst = newton_once(L, &s, deg, t1, gam, zh, o->lu_mode, o->max_refine, &res, &sw, fv, Jv,
+                              M, dz, &dzn, &zn);
+            it++;
+            if (nst != OR_OK) break;
+            conv = (res <= o->eps) || (dzn <= o->eps_x * (zn > 1.0 ? zn : 1.0));
+        }
+        nits += it;
+        if (!(nst == OR_OK && conv)) {
+            *fail_at = k;
+            status = OR_NOCONV;
+            break;
+        }
+        memcpy(zpp, zp, sizeof(C) * nc);
+        memcpy(zp, z, sizeof(C) * nc);
+        memcpy(z, zh, sizeof(C) * nc);
+        tpp = tp;
+        tp = t;
+        t = t1;
+        if (nhist < 3) nhist++;
+    }
+    double res_end = -1.0;
+    int end_its = 0;
+    if (status == OR_OK && t >= 1.0) {
+        double res = 1.0, dzn = 0.0, zn = 0.0;
+        int conv = 0;
+        while (!conv && end_its < o->end_it) {
+            int sw;
+            int nst = newton_once(L, &s, deg, 1.0, gam, z, o->lu_mode, o->max_refine, &res, &sw, fv,
+                                  Jv, M, dz, &dzn, &zn);
+            end_its++;
+            if (nst != OR_OK) { status = nst; break; }
+            conv = (res <= o->eps_end) || (dzn <= o->eps_end_x * (zn > 1.0 ? zn : 1.0));
+        }
+        res_end = res;
+        if (status == OR_OK && !conv) status = OR_NOCONV;
+    }
+    for (int j = 0; j < n; j++) c_store(L, z[j], x1 + (size_t)j * 2 * L);
+    if (st) {
+        memset(st, 0, sizeof *st);
+        st->n_succ = nseq;
+        st->newton_its = nits;
+        st->t_end = t;
+        st->res_end = res_end;
+        st->status = status;
+        st->end_its = end_its;
+    }
+    free(deg); free(z); free(zp); free(zpp); free(zh); free(fv); free(Jv); free(M); free(dz);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------------------
  * Threaded batch driver for the CPU baseline: or_eval (mode 1) over points on nthreads
  * POSIX threads, each thread a contiguous block of points.

@@ -101,6 +101,10 @@ def lib():
                                    ct.POINTER(TrackOpts), _F64P, ct.POINTER(_Stats), p,
                                    ct.POINTER(ct.c_int32)]
             L.or_track.restype = i
+            L.or_track_replay.argtypes = [i, i, _I32P, _I32P, _I32P, _I32P, _F64P, _F64P, _F64P,
+                                          ct.POINTER(TrackOpts), _F64P, i, _F64P,
+                                          ct.POINTER(ct.c_int32), ct.POINTER(_Stats)]
+            L.or_track_replay.restype = i
             _lib = L
     return _lib
 
@@ -276,3 +280,20 @@ def track(sysd, coef, x0, gamma, opts: TrackOpts, log_cap=0):
                               ("accepted", "i4")])
     return TrackResult(x1, st.status, st.n_succ, st.n_corr, st.newton_its, st.min_step,
                        st.avg_step, st.t_end, st.res_end, st.end_its, log)
+
+
+def track_replay(sysd, coef, x0, gamma, opts: TrackOpts, tseq):
+    """Follow the accepted parameter values tseq with the tracker's predictor and
+    corrector (and the end game).  Returns (end point, status, index of the first
+    rejected stage or -1)."""
+    L = coef.shape[-1]
+    n = sysd["n"]
+    x1 = np.zeros((n, 2, L))
+    st = _Stats()
+    fail = ct.c_int32(-1)
+    t = np.ascontiguousarray(tseq, dtype=np.float64)
+    rc = lib().or_track_replay(L, n, *_sysargs(sysd), _f64(coef), _f64(gamma), _f64(x0),
+                               ct.byref(opts), t, len(t), x1, ct.byref(fail), ct.byref(st))
+    if rc != 0:
+        raise ValueError(f"or_track_replay failed ({rc})")
+    return x1, st.status, fail.value

@@ -13,6 +13,7 @@
 
 #include <vector>
 
+#include "mlp.cuh"
 #include "path.cuh"
 
 namespace hc {
@@ -22,7 +23,32 @@ struct PathState {
     long long n_succ, n_corr, nits;
     int nhist, consec, status, phase;  // phase: 0 new, 1 tracking, 2 end game, 3 done
     int end_its, pad2;
+    // the last three corrector stages (index 0 = latest), for the step proposer
+    double hl[3], hr[3], pcd, cond;
+    int hi[3], pad3;
 };
+
+// Features of the step proposer before the next stage, each scaled to order one:
+//   0      t
+//   1..3   log2(lambda / lambda0) / 8 of the last three attempted steps
+//   4..6   their Newton iteration counts / 4
+//   7..9   log10 of their last residuals, clipped to [-40, 5], / 10
+//   10     log10 of the last predictor-corrector distance, clipped, / 10 (-4 after a
+//          rejection)
+//   11     log10 of the last condition estimate / 4
+// Missing history reads as steps of lambda0, 0 iterations, residual -40 (i.e. -4),
+// condition 0.
+__device__ __forceinline__ void proposer_features(const PathState &st, double lambda0, float *f)
+{
+    f[0] = (float)st.t;
+    for (int j = 0; j < 3; j++) {
+        f[1 + j] = (float)(log2(st.hl[j] / lambda0) / 8.0);
+        f[4 + j] = (float)(st.hi[j] / 4.0);
+        f[7 + j] = st.hr[j] > 0.0 ? (float)(fmin(fmax(log10(st.hr[j]), -40.0), 5.0) / 10.0) : -4.0f;
+    }
+    f[10] = st.pcd > 0.0 ? (float)(fmin(fmax(log10(st.pcd), -40.0), 5.0) / 10.0) : -4.0f;
+    f[11] = (float)(st.cond / 4.0);
+}
 
 struct SlotLayout {
     size_t pw, v, h, jh, b, rv, dz, zp, piv, stride;
@@ -99,6 +125,13 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
         st.status = HC_OK;
         st.phase = 1;
         st.end_its = 0;
+        for (int j = 0; j < 3; j++) {
+            st.hl[j] = o.lambda0;
+            st.hr[j] = 0.0;
+            st.hi[j] = 0;
+        }
+        st.pcd = -1.0;
+        st.cond = 0.0;
         __syncthreads();
     }
     int stages = 0;
@@ -201,6 +234,38 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
                 st.status = HC_MIN_STEP;
             }
         }
+        // history of the last three stages; with a proposer its estimate of the largest
+        // acceptable step sets the next one (the plain halving stays the fallback after a
+        // failure; the corrector still judges every step)
+        for (int j = 2; j > 0; j--) {
+            st.hl[j] = st.hl[j - 1];
+            st.hr[j] = st.hr[j - 1];
+            st.hi[j] = st.hi[j - 1];
+        }
+        st.hl[0] = h;
+        st.hr[0] = res;
+        st.hi[0] = it;
+        st.pcd = pcd;
+        st.cond = cond;
+        if (o.proposer && !stop) {
+            if (tid == 0) {
+                float f[MLP_IN];
+                proposer_features(st, o.lambda0, f);
+                sh.bc[0] = (double)mlp_forward_thread(o.proposer, f);
+            }
+            __syncthreads();
+            const double lam_p = h * exp2(sh.bc[0] - o.proposer_margin);
+            __syncthreads();
+            if (ok) {
+                st.lambda = fmin(fmax(lam_p, o.lambda_min), o.lambda_max);
+            } else {
+                st.lambda = fmin(st.lambda, lam_p);
+                if (st.lambda < o.lambda_min) {
+                    stop = 1;
+                    st.status = HC_MIN_STEP;
+                }
+            }
+        }
         if (!stop && st.t < 1.0 && st.n_corr >= o.max_steps) {
             stop = 1;
             st.status = HC_MAX_STEPS;
@@ -285,6 +350,8 @@ extern "C" void hc_track_opts_default(hc_track_opts *o)
     o->max_refine = 4;
     o->mode = HC_TRACK_PERSISTENT;
     o->graph_steps = 16;
+    o->proposer = NULL;
+    o->proposer_margin = 0.5;
 }
 
 static int check_opts(const hc_track_opts *o)
@@ -306,6 +373,8 @@ static int check_opts(const hc_track_opts *o)
         return hc_fail(HC_EINVAL, "unknown mode %d", o->mode);
     if (o->mode == HC_TRACK_GRAPH && (o->graph_steps < 1 || o->graph_steps > 1024))
         return hc_fail(HC_EINVAL, "graph_steps out of [1, 1024]");
+    if (o->proposer && !(o->proposer_margin >= 0.0 && o->proposer_margin < 64.0))
+        return hc_fail(HC_EINVAL, "proposer_margin out of [0, 64)");
     return HC_SUCCESS;
 }
 

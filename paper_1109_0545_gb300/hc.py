@@ -38,7 +38,7 @@ class TrackOpts(ct.Structure):
                 ("max_it", ct.c_int32), ("end_it", ct.c_int32), ("grow_after", ct.c_int32),
                 ("max_steps", ct.c_int32), ("predictor", ct.c_int32), ("lu_mode", ct.c_int32),
                 ("max_refine", ct.c_int32), ("mode", ct.c_int32), ("graph_steps", ct.c_int32),
-                ("reserved", ct.c_int32)]
+                ("reserved", ct.c_int32), ("proposer", ct.c_void_p), ("proposer_margin", ct.c_double)]
 
 
 class PathStats(ct.Structure):
@@ -101,6 +101,13 @@ def load(build_if_missing: bool = True):
         L.hc_track_path.argtypes = [ct.POINTER(vp), i, vp, vp, ct.POINTER(TrackOpts),
                                     ct.POINTER(PathStats), vp, i, vp]
         L.hc_track_path.restype = i
+        f = ct.c_float
+        L.hc_mlp_grad.argtypes = [vp, i, vp, vp, vp, f, vp, vp, vp]
+        L.hc_mlp_grad.restype = i
+        L.hc_mlp_adamw.argtypes = [vp, vp, vp, vp, i, f, f, f, f, f, vp]
+        L.hc_mlp_adamw.restype = i
+        L.hc_mlp_forward.argtypes = [vp, i, vp, vp, vp]
+        L.hc_mlp_forward.restype = i
         L.hc_eval_jac_noalloc.argtypes = [vp, i, d, vp, vp, vp, vp]
         L.hc_eval_jac_noalloc.restype = i
         L.hc_prof_enable.argtypes = [i]
@@ -242,6 +249,27 @@ def unpack_paths(buf: np.ndarray, dims: list[int], L: int) -> list[np.ndarray]:
         out.append(np.ascontiguousarray(np.transpose(buf[o:o + 2 * L * n].reshape(2, L, n), (2, 0, 1))))
         o += 2 * L * n
     return out
+
+
+HC_MLP_IN, HC_MLP_NPARAM = 12, 5057
+
+
+def hc_mlp_grad(params, nrec, feat, target, accepted, kappa, grad, loss=None, stream=None):
+    _check("hc_mlp_grad", load().hc_mlp_grad(_ptr(params), int(nrec), _ptr(feat), _ptr(target),
+                                             _ptr(accepted), float(kappa), _ptr(grad), _ptr(loss),
+                                             _stream(stream)))
+
+
+def hc_mlp_adamw(params, m1, m2, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=1e-4,
+                 stream=None):
+    _check("hc_mlp_adamw", load().hc_mlp_adamw(_ptr(params), _ptr(m1), _ptr(m2), _ptr(grad),
+                                               int(step), float(lr), float(beta1), float(beta2),
+                                               float(eps), float(wd), _stream(stream)))
+
+
+def hc_mlp_forward(params, nrec, feat, out, stream=None):
+    _check("hc_mlp_forward", load().hc_mlp_forward(_ptr(params), int(nrec), _ptr(feat), _ptr(out),
+                                                   _stream(stream)))
 
 
 def hc_probe_fp64_peak() -> float:
