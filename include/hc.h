@@ -139,6 +139,9 @@ int hc_set_tiles(int rows_per_task, int blocks_per_sm);
 #define HC_PRED_QUADRATIC 1  /* per coordinate, the parabola through the last three */
 #define HC_TRACK_PERSISTENT 0  /* one persistent kernel, paths from an atomic queue */
 #define HC_TRACK_GRAPH 1       /* one stage per launch, replayed as a CUDA graph */
+#define HC_TRACK_GRID 2        /* one path at a time on the whole GPU: each stage a CUDA
+                                  graph of grid-wide and single-block kernels (for
+                                  systems of ~1e5 monomials; HC_LU_FP64_REFINE only) */
 
 /* Options of hc_track_path.  The paper gives no constants (Alg. 3.1); the defaults of
  * hc_track_opts_default follow Tables 2-3: steps lambda0 * 2^j. */
@@ -165,7 +168,10 @@ typedef struct {
     int32_t reserved;
     const float *proposer;   /* device, HC_MLP_NPARAM weights of the learned step
                                 proposer, or NULL for the plain controller */
-    double proposer_margin;  /* the proposal is lambda_last * 2^(m - margin), 0.5 */
+    double proposer_margin;  /* the proposal is lambda_last * 2^(m - margin), 0.5; after
+                                an accepted stage it is clamped to [max(lambda_min,
+                                lambda_last / 2), lambda_max], after a rejection the
+                                smaller of it and the plain halving is taken */
 } hc_track_opts;
 
 /* Per-path result (the statistics of Tables 2-3). */
@@ -211,7 +217,8 @@ void hc_track_opts_default(hc_track_opts *opts);
  *   stats  host, npaths results, valid on return
  *   log    device, npaths * log_cap records (record s of path p at p * log_cap + s),
  *          or NULL with log_cap = 0
- * One thread block per path.  Synchronises the stream before returning.  Allocates and
+ * One thread block per path (HC_TRACK_GRID: the whole GPU per path, paths in turn).
+ * Synchronises the stream before returning.  Allocates and
  * frees its own workspace.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA, HC_ETIMEOUT (graph
  * mode only: paths still unfinished after max_steps / graph_steps + 2 replays).
  */

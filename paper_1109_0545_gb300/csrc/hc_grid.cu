@@ -1,0 +1,406 @@
+// hc_grid.cu -- one large path on the whole GPU (hc_track_path with HC_TRACK_GRID).
+//
+// A path whose system has ~10^5 monomials is too much for one thread block (one SM).
+// Here one predictor-corrector stage of Alg. 3.1 is a fixed sequence of kernels,
+// captured once as a CUDA graph and replayed by the host until the path ends:
+//
+//   begin (1 block)                      init, predictor (or end-game set-up)
+//   max_it x Newton iteration (Alg. 4.1):
+//     powers (1 block)                   x_j^e
+//     monomials (grid)                   values and partials of every monomial -> V
+//     entries (grid)                     sums per Jacobian entry + homotopy -> H, J
+//     factor (1 block)                   residual, FP64 LU with partial pivoting, dz_0
+//     max_refine x [residual rows (grid), solve (1 block)]    refinement in L limbs
+//     update (1 block)                   z += dz, convergence test
+//   end (1 block)                        accept / step back, step size, stop tests
+//
+// The control flow of the method is data dependent; every kernel first reads the stage
+// state and returns at once when its work is not needed (the corrector converged, the
+// refinement stopped, the path ended), so a fixed graph carries it.  No kernel waits on
+// another: kernel boundaries are the only synchronisation.
+#include <string.h>
+
+#include <vector>
+
+#include "track.cuh"
+
+namespace hc {
+
+struct GStage {
+    double t1, h, res, res_first, cond, dzn, zn, xn, prev_dn;
+    int it, conv, nst, allowed, refine_active, sweeps, pad[2];
+};
+
+struct GArgs {
+    DevSys S;
+    PathState *st;
+    GStage *g;
+    const double *x0;
+    double *z, *zp, *zpp, *zh, *ZP, *PW, *V, *H, *JH, *B, *RV, *DZ;
+    int32_t *PIV;
+    hc_track_opts o;
+    hc_step_record *log;
+    int log_cap;
+};
+
+__device__ __forceinline__ bool g_active(const GStage &g)
+{
+    return g.it < g.allowed && !g.conv && g.nst == HC_OK;
+}
+
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
+{
+    PathState st = *a.st;
+    GStage &g = *a.g;
+    const int n = a.S.n, tid = threadIdx.x;
+    if (st.phase == 0) {
+        for (int q = tid; q < 2 * L * n; q += HC_TB) a.z[q] = a.x0[q];
+        path_init(st, a.o);
+        __syncthreads();
+        if (tid == 0) *a.st = st;
+    }
+    __syncthreads();
+    if (st.phase == 1) {
+        double t1, h;
+        stage_predict<L>(a.o, st, n, a.z, a.zp, a.zpp, a.zh, a.ZP, t1, h);
+        if (tid == 0) {
+            g.t1 = t1;
+            g.h = h;
+            g.allowed = a.o.max_it;
+        }
+    } else if (st.phase == 2) {
+        for (int q = tid; q < 2 * L * n; q += HC_TB) a.zh[q] = a.z[q];
+        if (tid == 0) {
+            g.t1 = 1.0;
+            g.h = 0.0;
+            g.allowed = min(a.o.max_it, a.o.end_it - st.end_its);
+        }
+    } else if (tid == 0) {
+        g.allowed = 0;
+    }
+    if (tid == 0) {
+        g.it = 0;
+        g.conv = 0;
+        g.nst = HC_OK;
+        g.res = 1.0;
+        g.res_first = -1.0;
+        g.cond = 0.0;
+        g.refine_active = 0;
+    }
+}
+
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_powers(GArgs a)
+{
+    if (!g_active(*a.g)) return;
+    for (int j = threadIdx.x; j < a.S.n; j += HC_TB) powers_of<L>(a.S, j, a.zh, a.PW);
+}
+
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_monomials(GArgs a)
+{
+    if (!g_active(*a.g)) return;
+    const int q = blockIdx.x * HC_TB + threadIdx.x;
+    if (q < a.S.nmon) monomial_to_V<L>(a.S, __ldg(a.S.perm + q), a.zh, a.PW, a.V);
+}
+
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_entries(GArgs a)
+{
+    const GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int e = blockIdx.x * HC_TB + threadIdx.x;
+    const int ne = a.S.npoly * (a.S.n + 1);
+    if (e >= ne) return;
+    const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
+    entry_from_V<L>(a.S, e, a.zh, g.t1, gs, a.V, a.H, a.JH);
+}
+
+// residual of the incoming point, FP64 LU, first solve (block_newton's first half)
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a)
+{
+    __shared__ BlockShared sh;
+    GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int n = a.S.n, tid = threadIdx.x;
+    double r2 = 0.0;
+    int fin = 1;
+    for (int i = tid; i < n; i += HC_TB) {
+        double re, im;
+        ld_lead<L>(a.H, n, i, re, im);
+        const double v = add_(mul_(re, re), mul_(im, im));
+        if (!isfinite(v)) fin = 0;
+        r2 = fmax(r2, v);
+    }
+    fin = block_and(fin, sh);
+    const double res = sqrt(block_max(r2, sh));
+    double cond = 0.0;
+    int status = fin ? block_lu64<L>(n, a.JH, a.B, a.PIV, sh, &cond) : HC_NONFINITE;
+    if (status == HC_OK) {
+        for (int i = tid; i < n; i += HC_TB) {
+            double re, im;
+            ld_lead<L>(a.H, n, i, re, im);
+            a.RV[i] = -re;
+            a.RV[n + i] = -im;
+        }
+        __syncthreads();
+        block_lu64_solve(n, a.B, a.PIV, a.RV);
+        double xn = 0.0;
+        for (int i = tid; i < n; i += HC_TB) {
+            st_c<L>(a.DZ, n, i, c_from<L>(a.RV[i], a.RV[n + i]));
+            double re, im;
+            ld_lead<L>(a.zh, n, i, re, im);
+            xn = fmax(xn, sqrt(add_(mul_(re, re), mul_(im, im))));
+        }
+        xn = block_max(xn, sh);
+        if (tid == 0) g.xn = xn;
+    }
+    if (tid == 0) {
+        g.res = res;
+        if (g.res_first < 0) g.res_first = res;
+        g.cond = cond;
+        if (status != HC_OK) {
+            g.it++;
+            g.nst = status;
+        } else {
+            g.refine_active = a.o.max_refine > 0;
+            g.prev_dn = INFINITY;
+            g.sweeps = 0;
+        }
+    }
+}
+
+// r_i = -h_i - sum_j J_ij dz_j in L limbs, one block of 32 per row; each lane sums a
+// strided part of the row, then a fixed shuffle tree adds the 32 parts
+template <int L> __global__ void __launch_bounds__(32) k_g_refine_rows(GArgs a)
+{
+    const GStage &g = *a.g;
+    if (!g_active(g) || !g.refine_active) return;
+    const int n = a.S.n, i = blockIdx.x, lane = threadIdx.x;
+    C<L> acc = c_zero<L>();
+    for (int j = lane; j < n; j += 32)
+        acc = c_fnma(acc, ld_c<L>(a.JH, (size_t)n * n, (size_t)i * n + j), ld_c<L>(a.DZ, n, j));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        C<L> other;
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            other.re.v[l] = __shfl_down_sync(0xffffffffu, acc.re.v[l], o);
+            other.im.v[l] = __shfl_down_sync(0xffffffffu, acc.im.v[l], o);
+        }
+        acc = c_add(acc, other);
+    }
+    if (lane == 0) {
+        // acc = -sum_j J_ij dz_j, so r = acc - h_i
+        const C<L> r = c_sub(acc, ld_c<L>(a.H, n, i));
+        a.RV[i] = r.re.v[0];
+        a.RV[n + i] = r.im.v[0];
+    }
+}
+
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_refine_solve(GArgs a)
+{
+    __shared__ BlockShared sh;
+    GStage &g = *a.g;
+    if (!g_active(g) || !g.refine_active) return;
+    const int n = a.S.n, tid = threadIdx.x;
+    block_lu64_solve(n, a.B, a.PIV, a.RV);
+    double dn = 0.0, zz = 0.0;
+    for (int i = tid; i < n; i += HC_TB) {
+        const double dr = a.RV[i], di = a.RV[n + i];
+        const C<L> v = c_add(ld_c<L>(a.DZ, n, i), c_from<L>(dr, di));
+        st_c<L>(a.DZ, n, i, v);
+        dn = fmax(dn, sqrt(add_(mul_(dr, dr), mul_(di, di))));
+        zz = fmax(zz, sqrt(c_abs2_lead(v)));
+    }
+    dn = block_max(dn, sh);
+    zz = block_max(zz, sh);
+    if (tid == 0) {
+        g.sweeps++;
+        const double tol = ldexp(1.0, -53 * L);
+        if (dn <= tol * fmax(g.xn, zz) || dn >= g.prev_dn || g.sweeps >= a.o.max_refine) g.refine_active = 0;
+        g.prev_dn = dn;
+    }
+}
+
+// z += dz (all or nothing), the convergence test of the corrector or of the end game
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_update(GArgs a)
+{
+    __shared__ BlockShared sh;
+    GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int n = a.S.n, tid = threadIdx.x;
+    int ok = 1;
+    double dzn = 0.0, zn = 0.0;
+    for (int i = tid; i < n; i += HC_TB) {
+        const C<L> d = ld_c<L>(a.DZ, n, i);
+        const C<L> v = c_add(ld_c<L>(a.zh, n, i), d);
+        if (!c_finite_lead(v)) ok = 0;
+        dzn = fmax(dzn, sqrt(c_abs2_lead(d)));
+        zn = fmax(zn, sqrt(c_abs2_lead(v)));
+    }
+    ok = block_and(ok, sh);
+    dzn = block_max(dzn, sh);
+    zn = block_max(zn, sh);
+    if (ok)
+        for (int i = tid; i < n; i += HC_TB) st_c<L>(a.zh, n, i, c_add(ld_c<L>(a.zh, n, i), ld_c<L>(a.DZ, n, i)));
+    __syncthreads();
+    if (tid == 0) {
+        g.it++;
+        g.dzn = dzn;
+        g.zn = zn;
+        if (!ok) {
+            g.nst = HC_NONFINITE;
+        } else {
+            const bool end = a.st->phase == 2;
+            const double eps = end ? a.o.eps_end : a.o.eps, epsx = end ? a.o.eps_end_x : a.o.eps_x;
+            g.conv = (g.res <= eps) || (dzn <= epsx * (zn > 1.0 ? zn : 1.0));
+        }
+    }
+}
+
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_end(GArgs a)
+{
+    __shared__ BlockShared sh;
+    PathState st = *a.st;
+    const GStage g = *a.g;
+    const int n = a.S.n, tid = threadIdx.x;
+    if (st.phase == 1) {
+        stage_finish<L>(a.o, st, sh, n, a.z, a.zp, a.zpp, a.zh, a.ZP, g.t1, g.h, g.it, g.nst, g.conv, g.res,
+                        g.res_first, g.cond, a.log, a.log_cap);
+    } else if (st.phase == 2) {
+        for (int q = tid; q < 2 * L * n; q += HC_TB) a.z[q] = a.zh[q];
+        st.end_its += g.it;
+        if (g.nst != HC_OK) {
+            st.status = g.nst;
+            st.res_end = g.res;
+            st.phase = 3;
+        } else if (g.conv || st.end_its >= a.o.end_it) {
+            st.res_end = g.res;
+            if (!g.conv && st.status == HC_OK) st.status = HC_NOCONV;
+            st.phase = 3;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *a.st = st;
+}
+
+template <int L>
+static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t cs, cudaGraphExec_t *exec)
+{
+    const int mblocks = (a.S.nmon + HC_TB - 1) / HC_TB;
+    const int eblocks = (a.S.npoly * (a.S.n + 1) + HC_TB - 1) / HC_TB;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return hc_cuda_fail(e, "cudaStreamBeginCapture");
+    k_g_begin<L><<<1, HC_TB, 0, cs>>>(a);
+    for (int it = 0; it < max_it; it++) {
+        k_g_powers<L><<<1, HC_TB, 0, cs>>>(a);
+        k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_TB, 0, cs>>>(a);
+        k_g_entries<L><<<eblocks, HC_TB, 0, cs>>>(a);
+        k_g_factor<L><<<1, HC_TB, 0, cs>>>(a);
+        for (int r = 0; r < max_refine; r++) {
+            k_g_refine_rows<L><<<a.S.n, 32, 0, cs>>>(a);
+            k_g_refine_solve<L><<<1, HC_TB, 0, cs>>>(a);
+        }
+        k_g_update<L><<<1, HC_TB, 0, cs>>>(a);
+    }
+    k_g_end<L><<<1, HC_TB, 0, cs>>>(a);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return hc_cuda_fail(e, "capturing the stage graph");
+    return HC_SUCCESS;
+}
+
+}  // namespace hc
+
+using namespace hc;
+
+// One path per call to this function: workspace, graph, replays, statistics.
+int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const hc_track_opts *o,
+                       hc_path_stats *stats, hc_step_record *log, int log_cap, cudaStream_t st)
+{
+    const int n = s->n, L = s->prec;
+    const size_t vec = sizeof(double) * 2 * L * (size_t)n;
+    const size_t vplane = (size_t)s->nvar + s->nmon;
+    size_t off = 0;
+    auto put = [&](size_t b) { size_t at = off; off = hc_align256(off + b); return at; };
+    const size_t o_st = put(sizeof(PathState)), o_g = put(sizeof(GStage));
+    const size_t o_zp = put(vec), o_zpp = put(vec), o_zh = put(vec), o_ZP = put(vec);
+    const size_t o_pw = put(vec * (s->max_exp > 2 ? s->max_exp - 2 : 1));
+    const size_t o_v = put(sizeof(double) * 2 * L * (vplane > 0 ? vplane : 1));
+    const size_t o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n);
+    const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n);
+    void *ws = nullptr;
+    HC_CUDA_TRY(cudaMalloc(&ws, off));
+    char *b = (char *)ws;
+    GArgs a;
+    a.S = s->dev;
+    a.st = (PathState *)(b + o_st);
+    a.g = (GStage *)(b + o_g);
+    a.x0 = x0;
+    a.z = x1;
+    a.zp = (double *)(b + o_zp);
+    a.zpp = (double *)(b + o_zpp);
+    a.zh = (double *)(b + o_zh);
+    a.ZP = (double *)(b + o_ZP);
+    a.PW = (double *)(b + o_pw);
+    a.V = (double *)(b + o_v);
+    a.H = (double *)(b + o_h);
+    a.JH = (double *)(b + o_jh);
+    a.B = (double *)(b + o_b);
+    a.RV = (double *)(b + o_rv);
+    a.DZ = (double *)(b + o_dz);
+    a.PIV = (int32_t *)(b + o_piv);
+    a.o = *o;
+    a.log = log;
+    a.log_cap = log_cap;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = HC_SUCCESS;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, off, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+    if (e != cudaSuccess) rc = hc_cuda_fail(e, "grid tracker set-up");
+    if (!rc) {
+        if (L == 1) rc = grid_capture<1>(a, o->max_it, o->max_refine, cs, &exec);
+        else if (L == 2) rc = grid_capture<2>(a, o->max_it, o->max_refine, cs, &exec);
+        else rc = grid_capture<4>(a, o->max_it, o->max_refine, cs, &exec);
+    }
+    PathState hs;
+    memset(&hs, 0, sizeof hs);
+    // every replay is one corrector stage, or end-game iterations; the path ends within
+    // max_steps stages and end_it / max_it + 1 end-game replays
+    const long long limit = (long long)o->max_steps + o->end_it + 2;
+    for (long long r = 0; !rc && r < limit; r++) {
+        e = cudaGraphLaunch(exec, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, a.st, sizeof hs, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) rc = hc_cuda_fail(e, "stage graph replay");
+        if (hs.phase == 3) break;
+    }
+    if (!rc && hs.phase != 3) rc = hc_fail(HC_ETIMEOUT, "large path unfinished after the replay limit");
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ready) {
+        cudaEventRecord(ready, cs);
+        cudaStreamWaitEvent(st, ready, 0);
+        cudaEventDestroy(ready);
+    }
+    if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
+    cudaFree(ws);
+    if (rc) return rc;
+    stats->n_succ = hs.n_succ;
+    stats->n_corr = hs.n_corr;
+    stats->newton_its = hs.nits;
+    stats->min_step = hs.n_succ ? hs.minstep : 0.0;
+    stats->avg_step = hs.n_succ ? hs.sumstep / (double)hs.n_succ : 0.0;
+    stats->t_end = hs.t;
+    stats->res_end = hs.res_end;
+    stats->status = hs.status;
+    stats->end_its = hs.end_its;
+    return HC_SUCCESS;
+}

@@ -13,42 +13,9 @@
 
 #include <vector>
 
-#include "mlp.cuh"
-#include "path.cuh"
+#include "track.cuh"
 
 namespace hc {
-
-struct PathState {
-    double t, tp, tpp, lambda, minstep, sumstep, res_end, pad;
-    long long n_succ, n_corr, nits;
-    int nhist, consec, status, phase;  // phase: 0 new, 1 tracking, 2 end game, 3 done
-    int end_its, pad2;
-    // the last three corrector stages (index 0 = latest), for the step proposer
-    double hl[3], hr[3], pcd, cond;
-    int hi[3], pad3;
-};
-
-// Features of the step proposer before the next stage, each scaled to order one:
-//   0      t
-//   1..3   log2(lambda / lambda0) / 8 of the last three attempted steps
-//   4..6   their Newton iteration counts / 4
-//   7..9   log10 of their last residuals, clipped to [-40, 5], / 10
-//   10     log10 of the last predictor-corrector distance, clipped, / 10 (-4 after a
-//          rejection)
-//   11     log10 of the last condition estimate / 4
-// Missing history reads as steps of lambda0, 0 iterations, residual -40 (i.e. -4),
-// condition 0.
-__device__ __forceinline__ void proposer_features(const PathState &st, double lambda0, float *f)
-{
-    f[0] = (float)st.t;
-    for (int j = 0; j < 3; j++) {
-        f[1 + j] = (float)(log2(st.hl[j] / lambda0) / 8.0);
-        f[4 + j] = (float)(st.hi[j] / 4.0);
-        f[7 + j] = st.hr[j] > 0.0 ? (float)(fmin(fmax(log10(st.hr[j]), -40.0), 5.0) / 10.0) : -4.0f;
-    }
-    f[10] = st.pcd > 0.0 ? (float)(fmin(fmax(log10(st.pcd), -40.0), 5.0) / 10.0) : -4.0f;
-    f[11] = (float)(st.cond / 4.0);
-}
 
 struct SlotLayout {
     size_t pw, v, h, jh, b, rv, dz, zp, piv, stride;
@@ -87,13 +54,6 @@ template <int L> __device__ __forceinline__ Slot<L> slot_of(const TrackArgs &a, 
     return w;
 }
 
-// ||v||_inf from the leading limbs, the same value on every thread
-template <int L> __device__ __forceinline__ double vec_norm(int n, const double *v, BlockShared &sh)
-{
-    double m = 0.0;
-    for (int j = threadIdx.x; j < n; j += HC_TB) m = fmax(m, sqrt(c_abs2_lead(ld_c<L>(v, n, j))));
-    return block_max(m, sh);
-}
 
 //
 // Advance path p by at most max_stages corrector stages (then its end game, once t = 1).
@@ -114,58 +74,14 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
     if (st.phase == 3) return;
     if (st.phase == 0) {
         for (int q = tid; q < 2 * L * n; q += HC_TB) z[q] = a.x0[a.xoff[p] + q];
-        st.t = st.tp = st.tpp = 0.0;
-        st.lambda = o.lambda0;
-        st.minstep = INFINITY;
-        st.sumstep = 0.0;
-        st.res_end = -1.0;
-        st.n_succ = st.n_corr = st.nits = 0;
-        st.nhist = 1;
-        st.consec = 0;
-        st.status = HC_OK;
-        st.phase = 1;
-        st.end_its = 0;
-        for (int j = 0; j < 3; j++) {
-            st.hl[j] = o.lambda0;
-            st.hr[j] = 0.0;
-            st.hi[j] = 0;
-        }
-        st.pcd = -1.0;
-        st.cond = 0.0;
+        path_init(st, o);
         __syncthreads();
     }
+    hc_step_record *log = a.log ? a.log + (size_t)p * a.log_cap : nullptr;
     int stages = 0;
     while (st.phase == 1 && stages < max_stages) {
-        double t1 = add_(st.t, st.lambda);
-        if (t1 > 1.0) t1 = 1.0;
-        const double h = sub_(t1, st.t);
-        // predictor (Alg. 3.1 "predict"; Sec. 5 for the quadratic one)
-        if (o.predictor == HC_PRED_QUADRATIC && st.nhist >= 3) {
-            const double w0 = __ddiv_rn(mul_(sub_(t1, st.tp), sub_(t1, st.t)), mul_(sub_(st.tpp, st.tp), sub_(st.tpp, st.t)));
-            const double w1 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.t)), mul_(sub_(st.tp, st.tpp), sub_(st.tp, st.t)));
-            const double w2 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.tp)), mul_(sub_(st.t, st.tpp), sub_(st.t, st.tp)));
-            for (int j = tid; j < n; j += HC_TB) {
-                const C<L> v = c_add(c_add(c_mul_d(ld_c<L>(zpp, n, j), w0), c_mul_d(ld_c<L>(zp, n, j), w1)),
-                                     c_mul_d(ld_c<L>(z, n, j), w2));
-                st_c<L>(zh, n, j, v);
-                st_c<L>(w.ZP, n, j, v);
-            }
-        } else if (st.nhist >= 2) {
-            const double r = __ddiv_rn(h, sub_(st.t, st.tp));
-            for (int j = tid; j < n; j += HC_TB) {
-                const C<L> zj = ld_c<L>(z, n, j);
-                const C<L> v = c_add(zj, c_mul_d(c_sub(zj, ld_c<L>(zp, n, j)), r));
-                st_c<L>(zh, n, j, v);
-                st_c<L>(w.ZP, n, j, v);
-            }
-        } else {
-            for (int j = tid; j < n; j += HC_TB) {
-                const C<L> v = ld_c<L>(z, n, j);
-                st_c<L>(zh, n, j, v);
-                st_c<L>(w.ZP, n, j, v);
-            }
-        }
-        __syncthreads();
+        double t1, h;
+        stage_predict<L>(o, st, n, z, zp, zpp, zh, w.ZP, t1, h);
         // corrector: Alg. 4.1
         double res = 1.0, res_first = -1.0, cond = 0.0;
         int it = 0, nst = HC_OK, conv = 0;
@@ -179,102 +95,8 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
             if (nst != HC_OK) break;
             conv = (res <= o.eps) || (no.dzn <= o.eps_x * (no.zn > 1.0 ? no.zn : 1.0));
         }
-        st.nits += it;
-        st.n_corr++;
-        int ok = (nst == HC_OK) && conv;
-        const double znorm = vec_norm<L>(n, zh, sh);
-        int stop = 0;
-        if (ok && !(znorm <= o.div_bound)) {
-            ok = 0;
-            st.status = isfinite(znorm) ? HC_DIVERGED : HC_NONFINITE;
-            stop = 1;
-        }
-        double pcd = -1.0;
-        if (ok) {
-            double m = 0.0;
-            for (int j = tid; j < n; j += HC_TB)
-                m = fmax(m, sqrt(c_abs2_lead(c_sub(ld_c<L>(zh, n, j), ld_c<L>(w.ZP, n, j)))));
-            pcd = block_max(m, sh);
-        }
-        if (a.log && tid == 0 && st.n_corr <= a.log_cap) {
-            hc_step_record &r = a.log[(size_t)p * a.log_cap + (st.n_corr - 1)];
-            r.t = st.t;
-            r.lambda = h;
-            r.res_first = res_first;
-            r.res_last = res;
-            r.pc_dist = pcd;
-            r.cond_log10 = cond;
-            r.iters = it;
-            r.accepted = ok;
-        }
-        if (ok) {
-            for (int j = tid; j < n; j += HC_TB) {
-                st_c<L>(zpp, n, j, ld_c<L>(zp, n, j));
-                st_c<L>(zp, n, j, ld_c<L>(z, n, j));
-                st_c<L>(z, n, j, ld_c<L>(zh, n, j));
-            }
-            st.tpp = st.tp;
-            st.tp = st.t;
-            st.t = t1;
-            if (st.nhist < 3) st.nhist++;
-            st.n_succ++;
-            st.sumstep = add_(st.sumstep, h);
-            if (h < st.minstep) st.minstep = h;
-            st.consec++;
-            if (st.consec >= o.grow_after) {
-                st.lambda = mul_(st.lambda, o.grow);
-                if (st.lambda > o.lambda_max) st.lambda = o.lambda_max;
-                st.consec = 0;
-            }
-        } else if (!stop) {
-            st.consec = 0;
-            st.lambda = mul_(st.lambda, o.shrink);
-            if (st.lambda < o.lambda_min) {
-                stop = 1;
-                st.status = HC_MIN_STEP;
-            }
-        }
-        // history of the last three stages; with a proposer its estimate of the largest
-        // acceptable step sets the next one (the plain halving stays the fallback after a
-        // failure; the corrector still judges every step)
-        for (int j = 2; j > 0; j--) {
-            st.hl[j] = st.hl[j - 1];
-            st.hr[j] = st.hr[j - 1];
-            st.hi[j] = st.hi[j - 1];
-        }
-        st.hl[0] = h;
-        st.hr[0] = res;
-        st.hi[0] = it;
-        st.pcd = pcd;
-        st.cond = cond;
-        if (o.proposer && !stop) {
-            if (tid == 0) {
-                float f[MLP_IN];
-                proposer_features(st, o.lambda0, f);
-                sh.bc[0] = (double)mlp_forward_thread(o.proposer, f);
-            }
-            __syncthreads();
-            const double lam_p = h * exp2(sh.bc[0] - o.proposer_margin);
-            __syncthreads();
-            if (ok) {
-                st.lambda = fmin(fmax(lam_p, o.lambda_min), o.lambda_max);
-            } else {
-                st.lambda = fmin(st.lambda, lam_p);
-                if (st.lambda < o.lambda_min) {
-                    stop = 1;
-                    st.status = HC_MIN_STEP;
-                }
-            }
-        }
-        if (!stop && st.t < 1.0 && st.n_corr >= o.max_steps) {
-            stop = 1;
-            st.status = HC_MAX_STEPS;
-        }
-        __syncthreads();
-        if (stop)
-            st.phase = 3;
-        else if (st.t >= 1.0)
-            st.phase = 2;
+        stage_finish<L>(o, st, sh, n, z, zp, zpp, zh, w.ZP, t1, h, it, nst, conv, res, res_first, cond,
+                        log, a.log_cap);
         stages++;
     }
     if (st.phase == 2) {
@@ -327,6 +149,9 @@ __global__ void __launch_bounds__(HC_TB) k_track(TrackArgs a, int persistent)
 
 using namespace hc;
 
+int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const hc_track_opts *o,
+                       hc_path_stats *stats, hc_step_record *log, int log_cap, cudaStream_t st);
+
 extern "C" void hc_track_opts_default(hc_track_opts *o)
 {
     if (!o) return;
@@ -369,8 +194,10 @@ static int check_opts(const hc_track_opts *o)
         return hc_fail(HC_EINVAL, "unknown lu_mode %d", o->lu_mode);
     if (o->lu_mode == HC_LU_FP64_REFINE && (o->max_refine < 1 || o->max_refine > 64))
         return hc_fail(HC_EINVAL, "max_refine out of [1, 64]");
-    if (o->mode != HC_TRACK_PERSISTENT && o->mode != HC_TRACK_GRAPH)
+    if (o->mode != HC_TRACK_PERSISTENT && o->mode != HC_TRACK_GRAPH && o->mode != HC_TRACK_GRID)
         return hc_fail(HC_EINVAL, "unknown mode %d", o->mode);
+    if (o->mode == HC_TRACK_GRID && o->lu_mode != HC_LU_FP64_REFINE)
+        return hc_fail(HC_EINVAL, "HC_TRACK_GRID runs the FP64 LU with refinement (HC_LU_FP64_REFINE)");
     if (o->mode == HC_TRACK_GRAPH && (o->graph_steps < 1 || o->graph_steps > 1024))
         return hc_fail(HC_EINVAL, "graph_steps out of [1, 1024]");
     if (o->proposer && !(o->proposer_margin >= 0.0 && o->proposer_margin < 64.0))
@@ -425,6 +252,16 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         emax = s->max_exp > emax ? s->max_exp : emax;
         const long long v = (long long)s->nvar + s->nmon;
         vmax = v > vmax ? v : vmax;
+    }
+    if (opts->mode == HC_TRACK_GRID) {
+        // one path at a time, each on the whole GPU
+        for (int p = 0; p < npaths; p++) {
+            rc = hc_track_grid_path(sys[p], x0 + off[p], x1 + off[p], opts, &stats[p],
+                                    log_cap > 0 ? log + (size_t)p * log_cap : nullptr, log_cap,
+                                    (cudaStream_t)stream);
+            if (rc) return rc;
+        }
+        return HC_SUCCESS;
     }
     const int sms = hc_num_sms();
     int occ = L == 1 ? occupancy_track<1>() : L == 2 ? occupancy_track<2>() : occupancy_track<4>();

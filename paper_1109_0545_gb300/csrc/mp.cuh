@@ -95,14 +95,14 @@ template <int L> __device__ __forceinline__ R<L> r_neg(R<L> a)
 // Five components of roughly decreasing magnitude -> four nonoverlapping limbs.
 // Bottom-up two-sums carry the value up exactly (two-sums, not fast-two-sums: after a
 // cancellation the components need not be ordered); the top-down fast-two-sums then
-// re-split it (a zero component bubbles down: fast_two_sum(0, b) = (b, 0)).  34 FP64.
+// re-split it (a zero component bubbles down: fast_two_sum(0, b) = (b, 0)).  22 FP64.
 __device__ __forceinline__ R<4> renorm5(double c0, double c1, double c2, double c3, double c4)
 {
     double s, t3, t2, t1, t0;
-    two_sum(c3, c4, s, t3);
-    two_sum(c2, s, s, t2);
-    two_sum(c1, s, s, t1);
-    two_sum(c0, s, c0, t0);
+    two_sum_ord(c3, c4, s, t3);
+    two_sum_ord(c2, s, s, t2);
+    two_sum_ord(c1, s, s, t1);
+    two_sum_ord(c0, s, c0, t0);
     R<4> r;
     double e;
     fast_two_sum(c0, t0, r.v[0], e);
@@ -131,17 +131,17 @@ __device__ __forceinline__ R<2> r_add(R<2> a, R<2> b)
     fast_two_sum(s, e, r.v[0], r.v[1]);
     return r;
 }
-// quad-double: limb-wise two-sums, errors cascaded one order down, renormalised.  ~71 FP64.
+// quad-double: limb-wise two-sums, errors cascaded one order down, renormalised.  47 FP64.
 __device__ __forceinline__ R<4> r_add(R<4> a, R<4> b)
 {
     double s0, s1, s2, s3, t0, t1, t2, t3, u, w;
-    two_sum(a.v[0], b.v[0], s0, t0);
-    two_sum(a.v[1], b.v[1], s1, t1);
-    two_sum(a.v[2], b.v[2], s2, t2);
-    two_sum(a.v[3], b.v[3], s3, t3);
-    two_sum(s1, t0, s1, t0);           // order 1 -> s1, order-2 error t0
-    two_sum(s2, t1, s2, u);            // order 2: s2 + t1 + t0
-    two_sum(s2, t0, s2, w);
+    two_sum_ord(a.v[0], b.v[0], s0, t0);
+    two_sum_ord(a.v[1], b.v[1], s1, t1);
+    two_sum_ord(a.v[2], b.v[2], s2, t2);
+    two_sum_ord(a.v[3], b.v[3], s3, t3);
+    two_sum_ord(s1, t0, s1, t0);           // order 1 -> s1, order-2 error t0
+    two_sum_ord(s2, t1, s2, u);            // order 2: s2 + t1 + t0
+    two_sum_ord(s2, t0, s2, w);
     double c3 = add_(add_(add_(s3, t2), add_(u, w)), t3);  // order 3
     return renorm5(s0, s1, s2, c3, 0.0);
 }
@@ -167,7 +167,7 @@ __device__ __forceinline__ R<2> r_mul(R<2> a, R<2> b)
     return r;
 }
 // quad-double: products of order 0..2 exact, order 3 rounded, order 4 dropped; each
-// order summed with two-sums whose errors fall into the next order.  ~107 FP64.
+// order summed with two-sums whose errors fall into the next order.  71 FP64.
 __device__ __forceinline__ R<4> r_mul(R<4> a, R<4> b)
 {
     double p00, e00, p01, e01, p10, e10, p02, e02, p11, e11, p20, e20;
@@ -178,15 +178,15 @@ __device__ __forceinline__ R<4> r_mul(R<4> a, R<4> b)
     two_prod(a.v[1], b.v[1], p11, e11);
     two_prod(a.v[2], b.v[0], p20, e20);
     double c1, u1, u2, s;
-    two_sum(p01, p10, s, u1);
-    two_sum(s, e00, c1, u2);                       // order 1
+    two_sum_ord(p01, p10, s, u1);
+    two_sum_ord(s, e00, c1, u2);                       // order 1
     double c2, v1, v2, v3, v4, v5, v6;
-    two_sum(p02, p11, s, v1);
-    two_sum(s, p20, s, v2);
-    two_sum(s, e01, s, v3);
-    two_sum(s, e10, s, v4);
-    two_sum(s, u1, s, v5);
-    two_sum(s, u2, c2, v6);                        // order 2
+    two_sum_ord(p02, p11, s, v1);
+    two_sum_ord(s, p20, s, v2);
+    two_sum_ord(s, e01, s, v3);
+    two_sum_ord(s, e10, s, v4);
+    two_sum_ord(s, u1, s, v5);
+    two_sum_ord(s, u2, c2, v6);                        // order 2
     double c3 = fma_(a.v[0], b.v[3], fma_(a.v[1], b.v[2], fma_(a.v[2], b.v[1], mul_(a.v[3], b.v[0]))));
     c3 = add_(c3, add_(add_(e02, e11), e20));
     c3 = add_(c3, add_(add_(add_(v1, v2), add_(v3, v4)), add_(v5, v6)));  // order 3
@@ -211,10 +211,10 @@ __device__ __forceinline__ R<4> r_mul_d(R<4> a, double d)
     two_prod(a.v[1], d, p1, e1);
     two_prod(a.v[2], d, p2, e2);
     double c1, u;
-    two_sum(p1, e0, c1, u);
+    two_sum_ord(p1, e0, c1, u);
     double c2, w1, w2;
-    two_sum(p2, e1, c2, w1);
-    two_sum(c2, u, c2, w2);
+    two_sum_ord(p2, e1, c2, w1);
+    two_sum_ord(c2, u, c2, w2);
     double c3 = fma_(a.v[3], d, add_(add_(e2, w1), w2));
     return renorm5(p0, c1, c2, c3, 0.0);
 }

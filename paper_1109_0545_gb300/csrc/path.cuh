@@ -93,74 +93,98 @@ __device__ __forceinline__ void block_argmax(double &v, int &i, BlockShared &sh)
 //   2. entry-parallel: each thread owns entries (i, j) and adds their contributions in
 //      the original monomial order (transpose table), then assembles the homotopy.
 //
+// Phase 1 for one monomial m: its value c x^a (slot nvar + m of V) and its scaled
+// partials a_j c x^(a - e_j) (slots var_ptr[m] + j), by the common factor with the
+// coefficient folded in, prefix products and a backward sweep (as in points.cuh).
+template <int L>
+__device__ __forceinline__ void monomial_to_V(const DevSys &S, int m, const double *__restrict__ z,
+                                              const double *__restrict__ PW, double *__restrict__ V)
+{
+    const int n = S.n;
+    const size_t vplane = (size_t)S.nvar + S.nmon;
+    auto X = [&](int j) { return ld_c<L>(z, n, j); };
+    auto P = [&](int j, int e) { return e == 1 ? X(j) : ld_c<L>(PW + (size_t)(e - 2) * 2 * L * n, n, j); };
+    const int q0 = __ldg(S.var_ptr + m), k = __ldg(S.var_ptr + m + 1) - q0;
+    const C<L> c = ld_c<L>(S.coef + (size_t)m * 2 * L, 1, 0);
+    if (k == 0) {
+        st_c<L>(V, vplane, (size_t)S.nvar + m, c);
+        return;
+    }
+    C<L> pre[HC_KLOCAL];
+    C<L> cf = c;
+    for (int j = 0; j < k; j++) {
+        const int pk = __ldg(S.var_pack + q0 + j);
+        if ((pk >> 16) >= 2) cf = c_mul_nn(cf, P(pk & 0xffff, (pk >> 16) - 1));
+    }
+    pre[0] = cf;
+    for (int j = 1; j < k; j++) pre[j] = c_mul_nn(pre[j - 1], X(__ldg(S.var_pack + q0 + j - 1) & 0xffff));
+    const int pkl = __ldg(S.var_pack + q0 + k - 1);
+    const C<L> xl = X(pkl & 0xffff);
+    st_c<L>(V, vplane, (size_t)S.nvar + m, c_mul_nn(pre[k - 1], xl));
+    st_c<L>(V, vplane, (size_t)q0 + k - 1, c_scale_int(pre[k - 1], pkl >> 16));
+    C<L> suf = xl;
+    for (int j = k - 2; j >= 0; j--) {
+        const int pk = __ldg(S.var_pack + q0 + j);
+        st_c<L>(V, vplane, (size_t)q0 + j, c_scale_int(c_mul_nn(pre[j], suf), pk >> 16));
+        if (j > 0) suf = c_mul_nn(suf, X(pk & 0xffff));
+    }
+}
+
+// power table of the point z: PW[e-2] = z^e, e = 2 .. max_exp-1, for variable j
+template <int L>
+__device__ __forceinline__ void powers_of(const DevSys &S, int j, const double *__restrict__ z, double *__restrict__ PW)
+{
+    const int n = S.n;
+    const C<L> x = ld_c<L>(z, n, j);
+    C<L> v = x;
+    for (int e = 2; e < S.max_exp; e++) {
+        v = c_mul(v, x);
+        st_c<L>(PW + (size_t)(e - 2) * 2 * L * n, n, j, v);
+    }
+}
+
+// Phase 2 for one entry e = i (n+1) + j: the sum of its contributions in the original
+// monomial order, then the homotopy (t >= 0); j == n is h_i, else dh_i/dx_j.
+template <int L>
+__device__ __forceinline__ void entry_from_V(const DevSys &S, int e, const double *__restrict__ z, double t,
+                                             const C<L> &gs, const double *__restrict__ V,
+                                             double *__restrict__ H, double *__restrict__ JH)
+{
+    const int n = S.n;
+    const size_t vplane = (size_t)S.nvar + S.nmon;
+    const int i = e / (n + 1), j = e - i * (n + 1);
+    C<L> acc = c_zero<L>();
+    const int r1 = __ldg(S.tptr + e + 1);
+    for (int r = __ldg(S.tptr + e); r < r1; r++) acc = c_add(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
+    if (t >= 0.0) {
+        const int d = __ldg(S.deg + i);
+        const C<L> xi = ld_c<L>(z, n, i);
+        if (j == n) {
+            C<L> g = c_mul(c_pow(xi, d - 1), xi);
+            g.re = r_sub(g.re, r_from<L>(1.0));
+            acc = c_add(c_mul(gs, g), c_mul_d(acc, t));
+        } else {
+            acc = c_mul_d(acc, t);
+            if (i == j) acc = c_add(acc, c_mul(gs, c_scale_int(c_pow(xi, d - 1), d)));
+        }
+    }
+    if (j == n)
+        st_c<L>(H, n, i, acc);
+    else
+        st_c<L>(JH, (size_t)n * n, (size_t)i * n + j, acc);
+}
+
 template <int L>
 __device__ void block_eval(const DevSys &S, const double *__restrict__ z, double t, const Slot<L> &w)
 {
     const int n = S.n, tid = threadIdx.x;
-    const size_t vplane = (size_t)S.nvar + S.nmon;
-    for (int j = tid; j < n; j += HC_TB) {
-        const C<L> x = ld_c<L>(z, n, j);
-        C<L> v = x;
-        for (int e = 2; e < S.max_exp; e++) {
-            v = c_mul(v, x);
-            st_c<L>(w.PW + (size_t)(e - 2) * 2 * L * n, n, j, v);
-        }
-    }
+    for (int j = tid; j < n; j += HC_TB) powers_of<L>(S, j, z, w.PW);
     __syncthreads();
-    auto X = [&](int j) { return ld_c<L>(z, n, j); };
-    auto P = [&](int j, int e) { return e == 1 ? X(j) : ld_c<L>(w.PW + (size_t)(e - 2) * 2 * L * n, n, j); };
-    C<L> pre[HC_KLOCAL];
-    for (int q = tid; q < S.nmon; q += HC_TB) {
-        const int m = __ldg(S.perm + q);
-        const int q0 = __ldg(S.var_ptr + m), k = __ldg(S.var_ptr + m + 1) - q0;
-        const C<L> c = ld_c<L>(S.coef + (size_t)m * 2 * L, 1, 0);
-        if (k == 0) {
-            st_c<L>(w.V, vplane, (size_t)S.nvar + m, c);
-            continue;
-        }
-        C<L> cf = c;
-        for (int j = 0; j < k; j++) {
-            const int pk = __ldg(S.var_pack + q0 + j);
-            if ((pk >> 16) >= 2) cf = c_mul_nn(cf, P(pk & 0xffff, (pk >> 16) - 1));
-        }
-        pre[0] = cf;
-        for (int j = 1; j < k; j++) pre[j] = c_mul_nn(pre[j - 1], X(__ldg(S.var_pack + q0 + j - 1) & 0xffff));
-        const int pkl = __ldg(S.var_pack + q0 + k - 1);
-        const C<L> xl = X(pkl & 0xffff);
-        st_c<L>(w.V, vplane, (size_t)S.nvar + m, c_mul_nn(pre[k - 1], xl));
-        st_c<L>(w.V, vplane, (size_t)q0 + k - 1, c_scale_int(pre[k - 1], pkl >> 16));
-        C<L> suf = xl;
-        for (int j = k - 2; j >= 0; j--) {
-            const int pk = __ldg(S.var_pack + q0 + j);
-            st_c<L>(w.V, vplane, (size_t)q0 + j, c_scale_int(c_mul_nn(pre[j], suf), pk >> 16));
-            if (j > 0) suf = c_mul_nn(suf, X(pk & 0xffff));
-        }
-    }
+    for (int q = tid; q < S.nmon; q += HC_TB) monomial_to_V<L>(S, __ldg(S.perm + q), z, w.PW, w.V);
     __syncthreads();
     const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
     const int ne = S.npoly * (n + 1);
-    for (int e = tid; e < ne; e += HC_TB) {
-        const int i = e / (n + 1), j = e - i * (n + 1);
-        C<L> acc = c_zero<L>();
-        const int r1 = __ldg(S.tptr + e + 1);
-        for (int r = __ldg(S.tptr + e); r < r1; r++) acc = c_add(acc, ld_c<L>(w.V, vplane, __ldg(S.tlist + r)));
-        if (t >= 0.0) {
-            const int d = __ldg(S.deg + i);
-            if (j == n) {
-                const C<L> xi = X(i);
-                C<L> g = c_mul(c_pow(xi, d - 1), xi);
-                g.re = r_sub(g.re, r_from<L>(1.0));
-                acc = c_add(c_mul(gs, g), c_mul_d(acc, t));
-            } else {
-                acc = c_mul_d(acc, t);
-                if (i == j) acc = c_add(acc, c_mul(gs, c_scale_int(c_pow(X(i), d - 1), d)));
-            }
-        }
-        if (j == n)
-            st_c<L>(w.H, n, i, acc);
-        else
-            st_c<L>(w.JH, (size_t)n * n, (size_t)i * n + j, acc);
-    }
+    for (int e = tid; e < ne; e += HC_TB) entry_from_V<L>(S, e, z, t, gs, w.V, w.H, w.JH);
     __syncthreads();
 }
 
@@ -301,7 +325,7 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
 }
 
 // solve with the FP64 LU: RV[2][n] in place
-__device__ void block_lu64_solve(int n, const double *__restrict__ B, const int32_t *__restrict__ PIV,
+static __device__ void block_lu64_solve(int n, const double *__restrict__ B, const int32_t *__restrict__ PIV,
                                  double *__restrict__ RV)
 {
     const int tid = threadIdx.x;

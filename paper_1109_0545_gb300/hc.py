@@ -52,7 +52,7 @@ STEP_RECORD_DTYPE = np.dtype([("t", "f8"), ("lam", "f8"), ("res_first", "f8"), (
                               ("pc_dist", "f8"), ("cond_log10", "f8"), ("iters", "i4"),
                               ("accepted", "i4")])
 HC_PRED_SECANT, HC_PRED_QUADRATIC = 0, 1
-HC_TRACK_PERSISTENT, HC_TRACK_GRAPH = 0, 1
+HC_TRACK_PERSISTENT, HC_TRACK_GRAPH, HC_TRACK_GRID = 0, 1, 2
 
 
 class HCError(RuntimeError):
