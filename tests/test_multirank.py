@@ -1,0 +1,51 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks, each with its own points,
+combine nothing but the slowest time (the only collective), and the whole-job value is
+the units of all ranks over that time."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_1109_0545_gb300 import synth
+    s, pts, _ = synth.eval_throughput(2, npts=64)
+    mine = bench.rank_points(rank, 64, s.n, pts)
+    ms = 100.0 + 50.0 * rank               # this rank's own time
+    tmax = bench.max_over_ranks(ms, dist)
+    out[rank] = (float(np.abs(mine).sum()), float(mine[0, 0].real), tmax)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_only_the_max_time():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    # both ranks see the slowest rank's time
+    assert res[0][2] == res[1][2] == 150.0
+    # the ranks work on different points of the same size (independent problems)
+    assert res[0][1] != res[1][1]
+    assert abs(res[0][0] - res[1][0]) < 1e-9 * res[0][0] + 1e-6  # |x| = 1 on the torus
+    # whole-job value: units of every rank over the job's (max) time
+    npts, steps = 64, 3
+    value = npts * world * steps / (res[0][2] * steps * 1e-3)
+    assert value == pytest.approx(npts * world / 0.150)
