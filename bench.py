@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--npts", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--profile-tracker", action="store_true",
+                    help="only run a short graph-stepped tracking of 8 uneven paths (for ncu)")
     return ap.parse_args()
 
 
@@ -180,15 +182,21 @@ def captured_traffic(npts: int):
     return per_pt * npts
 
 
+PROPOSER = os.path.join(ROOT, "paper_1109_0545_gb300", "data", "proposer_weights.npy")
+
+
 def tracker_bench(torch, hc, synth, npaths=128, plain_sample=2):
-    """Path steps/s of the batched tracker (all paths in one persistent kernel, FP64 LU
-    + DD refinement) against the plain GPU tracker (all-DD elimination, one path per
-    launch), on the uneven-path family (n 10..64, 20..200 monomials per polynomial,
-    k 2..8, exponents 1..3, seed 3) and on its regular variant (a pure power and a
-    constant per polynomial, so that paths end at regular roots); plus the secant
-    against the quadratic predictor (Sec. 5) on the regular variant."""
+    """Path steps/s and paths/s of the batched tracker (all paths in one persistent
+    kernel, FP64 LU + DD refinement; secant, quadratic, and quadratic + learned step
+    proposer) against the plain GPU tracker (all-DD elimination, secant, plain step
+    control, one path per launch), on the uneven-path family (n 10..64, 20..200
+    monomials per polynomial, k 2..8, exponents 1..3, seed 3) and on its regular
+    variant (a pure power and a constant per polynomial, so paths end at regular roots;
+    end points compared with the plain tracker's at 1e-28)."""
     import numpy as np
-    out = {}
+    prop = None
+    if os.path.exists(PROPOSER):
+        prop = torch.from_numpy(np.load(PROPOSER).astype(np.float32)).cuda()
 
     def run(systems, gammas, opts):
         handles = [hc.system_from(s, 2, g) for s, g in zip(systems, gammas)]
@@ -198,51 +206,71 @@ def tracker_bench(torch, hc, synth, npaths=128, plain_sample=2):
         t0 = time.perf_counter()
         stats = hc.hc_track_path(handles, x0, x1, opts)
         dt = time.perf_counter() - t0
+        ends = hc.unpack_paths(x1.cpu().numpy(), [s.n for s in systems], 2)
         for h in handles:
             h.free()
-        return stats, dt
+        return stats, ends, dt
 
-    fams = {"uneven": [synth.uneven_path_system(3, j) for j in range(npaths)]}
     rng = np.random.default_rng(33)
     reg = []
     for j in range(npaths):
         n = int(rng.integers(10, 65))
         reg.append((synth.regular_system(rng, n, (20, 200), (2, 8), (1, 3), lead=1),
                     synth.unit_complex(rng)))
-    fams["uneven_regular"] = reg
+    fams = {"uneven": [synth.uneven_path_system(3, j) for j in range(npaths)], "uneven_regular": reg}
+    variants = [("batched_secant", dict(lu_mode=hc.HC_LU_FP64_REFINE)),
+                ("batched_quadratic", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC))]
+    if prop is not None:
+        variants.append(("batched_quadratic_proposer",
+                         dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC,
+                              proposer=prop.data_ptr())))
+    out = {}
     for name, fam in fams.items():
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
-        ours = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE)
-        st, dt = run(systems, gammas, ours)
-        steps = sum(x["n_corr"] for x in st)
         plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE)
-        p_steps, p_dt = 0, 0.0
+        p_steps, p_dt, p_ends = 0, 0.0, []
         for j in range(plain_sample):
-            pst, pdt = run(systems[j:j + 1], gammas[j:j + 1], plain)
+            pst, pends, pdt = run(systems[j:j + 1], gammas[j:j + 1], plain)
             p_steps += pst[0]["n_corr"]
             p_dt += pdt
-        ok = [x for x in st if x["status"] == hc.HC_OK]
-        out[name] = {"paths": npaths, "batched_path_steps_per_s": steps / dt,
-                     "batched_paths_per_s": npaths / dt,
-                     "plain_path_steps_per_s": p_steps / p_dt,
-                     "plain_paths_per_s": plain_sample / p_dt,
-                     "plain_sample_paths": plain_sample,
-                     "speedup_steps": (steps / dt) / (p_steps / p_dt),
-                     "ok_paths": len(ok),
-                     "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
-    systems, gammas = [f[0] for f in reg], [f[1] for f in reg]
-    cmp = {}
-    for pred, nm in ((hc.HC_PRED_SECANT, "secant"), (hc.HC_PRED_QUADRATIC, "quadratic")):
-        st, dt = run(systems, gammas, hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE,
-                                                               predictor=pred))
-        ok = [x for x in st if x["status"] == hc.HC_OK]
-        cmp[nm] = {"mean_succ": float(np.mean([x["n_succ"] for x in ok])) if ok else None,
-                   "mean_corr": float(np.mean([x["n_corr"] for x in ok])) if ok else None,
-                   "mean_avg_step": float(np.mean([x["avg_step"] for x in ok])) if ok else None,
-                   "min_step": float(min(x["min_step"] for x in ok)) if ok else None,
-                   "ok_paths": len(ok), "seconds": dt}
-    out["predictors_regular"] = cmp
+        ref_st, ref_ends, _ = run(systems, gammas, hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE))
+        res = {"paths": npaths, "plain_one_path_per_launch": {
+            "path_steps_per_s": p_steps / p_dt, "paths_per_s": plain_sample / p_dt,
+            "sample_paths": plain_sample}}
+        for vname, kw in variants:
+            st, ends, dt = run(systems, gammas, hc.hc_track_opts_default(**kw))
+            steps = sum(x["n_corr"] for x in st)
+            same = sum(1 for p in range(npaths) if st[p]["status"] == hc.HC_OK and ref_st[p]["status"] == hc.HC_OK
+                       and np.abs((ends[p] - ref_ends[p]).sum(-1)).max()
+                       <= 1e-28 * max(1.0, np.abs(ref_ends[p].sum(-1)).max()))
+            res[vname] = {"path_steps_per_s": steps / dt, "paths_per_s": npaths / dt,
+                          "speedup_paths_vs_plain": (npaths / dt) / (plain_sample / p_dt),
+                          "mean_stages": steps / npaths,
+                          "ok_paths": sum(1 for x in st if x["status"] == hc.HC_OK),
+                          "same_end_point_as_plain_1e-28": same,
+                          "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
+        out[name] = res
     return out
+
+
+def rank_points(rank: int, npts: int, n: int, default):
+    """The points rank `rank` evaluates: rank 0 the workload's own, every other rank its
+    own seeded draw of the same size (independent problems: weak scaling)."""
+    import numpy as np
+    from paper_1109_0545_gb300 import synth
+    if rank == 0:
+        return default
+    return synth.torus_points(np.random.default_rng([2, rank]), npts, n)
+
+
+def max_over_ranks(ms: float, dist, device=None) -> float:
+    """The slowest rank's time (the job's time); the only collective of the bench."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def run_gpu(args):
@@ -266,8 +294,7 @@ def run_gpu(args):
     L = 2
     npts = args.npts
     s, pts, gamma = synth.eval_throughput(2, npts=npts)
-    if rank > 0:
-        pts = synth.torus_points(np.random.default_rng([2, rank]), npts, s.n)
+    pts = rank_points(rank, npts, s.n, pts)
     sysh = hc.system_from(s, L, gamma)
     stream = torch.cuda.current_stream()
     x0 = torch.from_numpy(hc.to_soa(pts, L)).cuda()
@@ -325,10 +352,7 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = sum(step_ms)
     eval_ms, eval_launches = hc.hc_prof_read()
-    if dist:
-        tmax = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        total_ms = float(tmax.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     value = npts * world * args.steps / (total_ms * 1e-3)
     status = st.cpu().numpy()
     sweeps = sw.cpu().numpy()
@@ -363,7 +387,24 @@ def run_gpu(args):
         J = torch.empty((2, L, s.npoly, s.n, npts), dtype=torch.float64, device="cuda")
         ms_eval = timed(lambda: hc.hc_eval_jac(sysh, npts, T_HOM, x, f, J, stream))
         del f, J
+        # complex QD evaluation throughput on 16,384 of the points
+        q = 16384
+        sysq = hc.system_from(s, 4, gamma)
+        xq = torch.from_numpy(hc.to_soa(pts[:q], 4)).cuda()
+        fq = torch.empty((2, 4, s.npoly, q), dtype=torch.float64, device="cuda")
+        Jq = torch.empty((2, 4, s.npoly, s.n, q), dtype=torch.float64, device="cuda")
+        hc.hc_eval_jac(sysq, q, T_HOM, xq, fq, Jq, stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        hc.hc_eval_jac(sysq, q, T_HOM, xq, fq, Jq, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_qd = ev0.elapsed_time(ev1)
+        sysq.free()
+        del xq, fq, Jq
         extras = {"tracker": tracker_bench(torch, hc, synth),
+                  "eval_jac_qd_points_per_s": q / (ms_qd * 1e-3),
+                  "eval_jac_qd_fp64_gops": opcount.eval_ops_per_point(s, 4) * q / (ms_qd * 1e-3) / 1e9,
                   "newton_native_dd_lu_points_per_s": npts / (ms_native * 1e-3),
                   "eval_jac_points_per_s": npts / (ms_eval * 1e-3),
                   "refine_sweeps_hist": np.bincount(sweeps, minlength=MAX_REFINE + 1).tolist(),
@@ -418,8 +459,30 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def profile_tracker():
+    """A short tracking run for profiling: 8 paths of the uneven-path family, graph mode
+    (one launch per stage), 6 corrector stages each."""
+    import numpy as np
+    import torch
+
+    from paper_1109_0545_gb300 import hc, synth
+    hc.load(build_if_missing=False)
+    fam = [synth.uneven_path_system(3, j) for j in range(8)]
+    handles = [hc.system_from(s, 2, g) for s, g in fam]
+    x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 2) for s, _ in fam])).cuda()
+    x1 = torch.zeros_like(x0)
+    o = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, mode=hc.HC_TRACK_GRAPH,
+                                 graph_steps=2, max_steps=6)
+    st = hc.hc_track_path(handles, x0, x1, o)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_tracker": [x["n_corr"] for x in st]}))
+
+
 def main():
     args = parse()
+    if args.profile_tracker:
+        profile_tracker()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -130,7 +130,8 @@ int hc_newton_step(hc_system *sys, int npts, double t, double *x, int lu_mode,
  * process (the autotuner's knob; 0 = automatic):
  *   rows_per_task  polynomials one warp evaluates per task (its 32 points each)
  *   blocks_per_sm  resident 4-warp blocks per SM of the persistent grid (<= 32)
- * Errors: HC_EINVAL.
+ * Process-wide host-side setting, not synchronised with calls in other threads; any
+ * setting gives the same results bit for bit.  Errors: HC_EINVAL.
  */
 int hc_set_tiles(int rows_per_task, int blocks_per_sm);
 
@@ -168,10 +169,12 @@ typedef struct {
     int32_t reserved;
     const float *proposer;   /* device, HC_MLP_NPARAM weights of the learned step
                                 proposer, or NULL for the plain controller */
-    double proposer_margin;  /* the proposal is lambda_last * 2^(m - margin), 0.5; after
-                                an accepted stage it is clamped to [max(lambda_min,
-                                lambda_last / 2), lambda_max], after a rejection the
-                                smaller of it and the plain halving is taken */
+    double proposer_margin;  /* the proposal is lambda_last * 2^(m - margin), 0.5.  The
+                                plain controller runs alongside on the same outcomes; its
+                                step lambda_p bounds the proposal: after an accepted
+                                stage to [max(lambda_min, lambda_p / 4), lambda_max],
+                                after a rejection to at most shrink * the step that
+                                failed, and MIN_STEP when that is below lambda_min */
 } hc_track_opts;
 
 /* Per-path result (the statistics of Tables 2-3). */
@@ -248,8 +251,9 @@ int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x
 
 /* grad[HC_MLP_NPARAM] = gradient of the mean loss over nrec records (feat[nrec][12],
  * target[nrec] = r, accepted[nrec]); *loss = the mean loss (loss may be NULL).  The
- * summation order is fixed: results are reproducible bit for bit.  Errors: HC_EINVAL,
- * HC_ENOMEM, HC_ECUDA. */
+ * summation order is fixed: results are reproducible bit for bit.  Keeps a process-wide
+ * workspace of per-block partial gradients (grown on demand, synchronising): calls must
+ * not overlap.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA. */
 int hc_mlp_grad(const float *params, int nrec, const float *feat, const float *target,
                 const int32_t *accepted, float kappa, float *grad, float *loss, void *stream);
 

@@ -204,10 +204,14 @@ extern "C" int hc_mlp_grad(const float *params, int nrec, const float *feat, con
         g_mlp_partial_bytes = need;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    static bool attr = false;
-    if (!attr) {
+    // the dynamic shared-memory limit is a per-device attribute of the kernel
+    static bool attr[64];
+    int dev = 0;
+    HC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return hc_fail(HC_EINVAL, "device %d beyond the 64 supported", dev);
+    if (!attr[dev]) {
         HC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
-        attr = true;
+        attr[dev] = true;
     }
     const float inv_n = 1.0f / (float)nrec;
     k_mlp_grad<<<nblk, MLP_THREADS, grad_smem(), st>>>(params, nrec, feat, target, accepted, kappa, inv_n,

@@ -414,6 +414,61 @@ template <> __device__ __forceinline__ C<2> c_fnma<2>(C<2> acc, C<2> l, C<2> b)
     return z;
 }
 
+// quad-double a*b + c*d as one sum: products of order 0..2 exact (two-products), order 3
+// rounded, order 4 dropped; each order summed by ordered two-sums whose errors fall into
+// the next order; one renormalisation.  141 FP64 (4 products and 2 sums: 378 for the
+// complex product's two parts together, 282 this way).
+__device__ __forceinline__ R<4> qd_dot2(const R<4> &a, const R<4> &b, const R<4> &c, const R<4> &d)
+{
+    double p0, e0, q0, f0, s0, u;
+    two_prod(a.v[0], b.v[0], p0, e0);
+    two_prod(c.v[0], d.v[0], q0, f0);
+    two_sum_ord(p0, q0, s0, u);
+    // order 1
+    double p01, e01, p10, e10, q01, f01, q10, f10;
+    two_prod(a.v[0], b.v[1], p01, e01);
+    two_prod(a.v[1], b.v[0], p10, e10);
+    two_prod(c.v[0], d.v[1], q01, f01);
+    two_prod(c.v[1], d.v[0], q10, f10);
+    double s1 = u, g1, g2, g3, g4, g5, g6;
+    two_sum_ord(s1, e0, s1, g1);
+    two_sum_ord(s1, f0, s1, g2);
+    two_sum_ord(s1, p01, s1, g3);
+    two_sum_ord(s1, p10, s1, g4);
+    two_sum_ord(s1, q01, s1, g5);
+    two_sum_ord(s1, q10, s1, g6);
+    // order 2
+    double p02, e02, p11, e11, p20, e20, q02, f02, q11, f11, q20, f20;
+    two_prod(a.v[0], b.v[2], p02, e02);
+    two_prod(a.v[1], b.v[1], p11, e11);
+    two_prod(a.v[2], b.v[0], p20, e20);
+    two_prod(c.v[0], d.v[2], q02, f02);
+    two_prod(c.v[1], d.v[1], q11, f11);
+    two_prod(c.v[2], d.v[0], q20, f20);
+    const double o2[15] = {g2, g3, g4, g5, g6, e01, e10, f01, f10, p02, p11, p20, q02, q11, q20};
+    double s2 = g1, h = 0.0;
+#pragma unroll
+    for (int i = 0; i < 15; i++) {
+        double r;
+        two_sum_ord(s2, o2[i], s2, r);
+        h = add_(h, r);
+    }
+    // order 3
+    double s3 = fma_(a.v[0], b.v[3], fma_(a.v[1], b.v[2], fma_(a.v[2], b.v[1], mul_(a.v[3], b.v[0]))));
+    s3 = fma_(c.v[0], d.v[3], fma_(c.v[1], d.v[2], fma_(c.v[2], d.v[1], fma_(c.v[3], d.v[0], s3))));
+    s3 = add_(s3, add_(add_(add_(e02, e11), add_(e20, f02)), add_(f11, f20)));
+    s3 = add_(s3, h);
+    return renorm5(s0, s1, s2, s3, 0.0);
+}
+
+template <> __device__ __forceinline__ C<4> c_mul<4>(C<4> a, C<4> b)
+{
+    C<4> z;
+    z.re = qd_dot2(a.re, b.re, r_neg(a.im), b.im);
+    z.im = qd_dot2(a.re, b.im, a.im, b.re);
+    return z;
+}
+
 // 1 / b = conj(b) / |b|^2
 template <int L> __device__ __forceinline__ C<L> c_inv(C<L> b)
 {

@@ -155,6 +155,9 @@ __device__ __forceinline__ void entry_from_V(const DevSys &S, int e, const doubl
     const int i = e / (n + 1), j = e - i * (n + 1);
     C<L> acc = c_zero<L>();
     const int r1 = __ldg(S.tptr + e + 1);
+    // unrolled so that the gathers of several contributions are in flight together; the
+    // additions keep their order
+#pragma unroll 4
     for (int r = __ldg(S.tptr + e); r < r1; r++) acc = c_add(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
     if (t >= 0.0) {
         const int d = __ldg(S.deg + i);

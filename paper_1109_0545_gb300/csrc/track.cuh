@@ -16,6 +16,7 @@ struct PathState {
     // the last three corrector stages (index 0 = latest), for the step proposer
     double hl[3], hr[3], pcd, cond;
     int hi[3], pad3;
+    double lam_plain;  // the plain controller's step, run alongside the proposer
 };
 
 // Features of the step proposer before the next stage, each scaled to order one:
@@ -69,6 +70,7 @@ __device__ __forceinline__ void path_init(PathState &st, const hc_track_opts &o)
     }
     st.pcd = -1.0;
     st.cond = 0.0;
+    st.lam_plain = o.lambda0;
 }
 
 // Predictor (Alg. 3.1 "predict"; Sec. 5 for the quadratic one) at t1 = min(t + lambda, 1):
@@ -168,14 +170,16 @@ __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared 
             if (h < st.minstep) st.minstep = h;
             st.consec++;
             if (st.consec >= o.grow_after) {
-                st.lambda = mul_(st.lambda, o.grow);
-                if (st.lambda > o.lambda_max) st.lambda = o.lambda_max;
+                st.lam_plain = mul_(st.lam_plain, o.grow);
+                if (st.lam_plain > o.lambda_max) st.lam_plain = o.lambda_max;
                 st.consec = 0;
             }
+            st.lambda = st.lam_plain;
         } else if (!stop) {
             st.consec = 0;
-            st.lambda = mul_(st.lambda, o.shrink);
-            if (st.lambda < o.lambda_min) {
+            st.lam_plain = mul_(st.lam_plain, o.shrink);
+            st.lambda = st.lam_plain;
+            if (!o.proposer && st.lambda < o.lambda_min) {
                 stop = 1;
                 st.status = HC_MIN_STEP;
             }
@@ -202,12 +206,16 @@ __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared 
             __syncthreads();
             const double lam_p = h * exp2(sh.bc[0] - o.proposer_margin);
             __syncthreads();
+            // after a failure the step is at most shrink times the step that failed (the
+            // plain rule applied to the actual step); after a success the proposal may
+            // shrink the step ahead of a failure, but not below a quarter of the plain
+            // controller's step (lam_plain, run alongside on the same outcomes), so a path
+            // cannot crawl on tiny accepted steps
             if (ok) {
-                // after an accepted step the proposal may at most halve it (the plain
-                // controller's own worst case), so a pessimistic proposal cannot stall
-                st.lambda = fmin(fmax(lam_p, fmax(o.lambda_min, 0.5 * h)), o.lambda_max);
+                st.lambda = fmin(fmax(lam_p, fmax(o.lambda_min, 0.25 * st.lam_plain)), o.lambda_max);
             } else {
-                st.lambda = fmin(st.lambda, lam_p);
+                // the stop criterion follows the actual step
+                st.lambda = fmin(mul_(h, o.shrink), lam_p);
                 if (st.lambda < o.lambda_min) {
                     stop = 1;
                     st.status = HC_MIN_STEP;

@@ -137,6 +137,7 @@ def evaluate(torch, systems, gammas, params, margin=0.5, lu_mode=hc.HC_LU_FP64_R
         out[name] = {"stats": st, "ends": ends, "seconds": dt,
                      "mean_stages": float(np.mean([x["n_corr"] for x in st])),
                      "mean_rejected": float(np.mean([x["n_corr"] - x["n_succ"] for x in st])),
+                     "mean_newton_its": float(np.mean([x["newton_its"] for x in st])),
                      "ok_paths": int(np.sum(ok)),
                      "stages_per_s": float(sum(x["n_corr"] for x in st) / dt),
                      "paths_per_s": len(systems) / dt}
@@ -162,6 +163,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--out", default="proposer_result.json")
     ap.add_argument("--weights", default="proposer_weights.npy")
+    ap.add_argument("--uneven-eval-paths", type=int, default=512)
+    ap.add_argument("--margins", default="0.5")
     args = ap.parse_args()
     import torch
     hc.load(build_if_missing=False)
@@ -169,21 +172,30 @@ def main():
     t0 = time.perf_counter()
     Xs, rs, as_ = [], [], []
     total, j = 0, 0
-    # logs of the plain tracker on the uneven-path family, seeds 10..19
+    # logs of the plain tracker, seeds 10..19: the uneven-path family and its regular
+    # variant in equal parts (the family as drawn has no regular end points: every path
+    # there ends at a singular root or at infinity, so its logs alone teach only the
+    # approach to those)
     while total < args.records:
         systems, gammas = [], []
         for seed in range(10, 20):
-            for k in range(32):
+            for k in range(16):
                 s, g = synth.uneven_path_system(seed, j + k)
                 systems.append(s)
                 gammas.append(g)
-        j += 32
+            for s, g in regular_family(1000 * seed + j, 16):
+                systems.append(s)
+                gammas.append(g)
+        j += 16
         X, r, a = collect(torch, systems, gammas, plain)
         Xs.append(X)
         rs.append(r)
         as_.append(a)
         total += X.shape[0]
-    X, r, a = np.concatenate(Xs)[:args.records], np.concatenate(rs)[:args.records], np.concatenate(as_)[:args.records]
+    rng = np.random.default_rng(7)
+    X, r, a = np.concatenate(Xs), np.concatenate(rs), np.concatenate(as_)
+    keep = rng.permutation(X.shape[0])[:args.records]
+    X, r, a = X[keep], r[keep], a[keep]
     t_collect = time.perf_counter() - t0
     t0 = time.perf_counter()
     params, losses = train(torch, X, r, a, steps=args.steps)
@@ -193,21 +205,26 @@ def main():
     res = {"records": int(X.shape[0]), "accept_rate": float(a.mean()), "collect_s": t_collect,
            "train_s": t_train, "train_steps": args.steps, "loss_first": losses[0],
            "loss_last": losses[-1]}
-    for fam_name, fam in (("uneven_seed20", [synth.uneven_path_system(20, k) for k in range(args.eval_paths)]),
+    margins = [float(v) for v in args.margins.split(",")]
+    for fam_name, fam in (("uneven_seed20", [synth.uneven_path_system(20, k) for k in range(args.uneven_eval_paths)]),
                           ("uneven_regular_seed20", regular_family(20, args.eval_paths))):
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
-        ev = evaluate(torch, systems, gammas, params)
-        same = 0
-        both = 0
-        for p in range(len(systems)):
-            if ev["plain"]["stats"][p]["status"] == 0 and ev["proposer"]["stats"][p]["status"] == 0:
-                both += 1
-                d = np.abs((ev["plain"]["ends"][p] - ev["proposer"]["ends"][p]).sum(-1)).max()
-                same += d <= 1e-28 * max(1.0, np.abs(ev["plain"]["ends"][p].sum(-1)).max())
-        res[fam_name] = {k: {kk: vv for kk, vv in v.items() if kk not in ("stats", "ends")}
-                         for k, v in ev.items()}
-        res[fam_name]["both_ok"] = both
-        res[fam_name]["same_end_point_1e-28"] = int(same)
+        res[fam_name] = {}
+        for margin in margins:
+            ev = evaluate(torch, systems, gammas, params, margin=margin)
+            same = 0
+            both = 0
+            for p in range(len(systems)):
+                if ev["plain"]["stats"][p]["status"] == 0 and ev["proposer"]["stats"][p]["status"] == 0:
+                    both += 1
+                    d = np.abs((ev["plain"]["ends"][p] - ev["proposer"]["ends"][p]).sum(-1)).max()
+                    same += d <= 1e-28 * max(1.0, np.abs(ev["plain"]["ends"][p].sum(-1)).max())
+            r = {k: {kk: vv for kk, vv in v.items() if kk not in ("stats", "ends")} for k, v in ev.items()}
+            r["both_ok"] = both
+            r["same_end_point_1e-28"] = int(same)
+            r["status_plain"] = np.bincount([x["status"] for x in ev["plain"]["stats"]], minlength=7).tolist()
+            r["status_proposer"] = np.bincount([x["status"] for x in ev["proposer"]["stats"]], minlength=7).tolist()
+            res[fam_name][f"margin_{margin}"] = r
     with open(args.out, "w") as fh:
         json.dump(res, fh, indent=1)
     print(json.dumps(res))

@@ -12,8 +12,8 @@ from __future__ import annotations
 import numpy as np
 
 # FP64 instructions per operation, per limb count L
-C_MUL = {1: 4, 2: 32, 4: 4 * 71 + 2 * 47}       # normalised complex product
-C_MUL_NN = {1: 4, 2: 26, 4: 4 * 71 + 2 * 47}    # product feeding a product or a sum
+C_MUL = {1: 4, 2: 32, 4: 2 * 141}      # normalised complex product
+C_MUL_NN = {1: 4, 2: 26, 4: 2 * 141}   # product feeding a product or a sum
 C_ADD = {1: 2, 2: 16, 4: 2 * 47}
 R_ADD = {1: 1, 2: 8, 4: 47}
 C_MUL_D = {1: 2, 2: 12, 4: 2 * 40}
