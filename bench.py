@@ -185,14 +185,16 @@ def captured_traffic(npts: int):
 PROPOSER = os.path.join(ROOT, "paper_1109_0545_gb300", "data", "proposer_weights.npy")
 
 
-def tracker_bench(torch, hc, synth, npaths=128, plain_sample=2):
+def tracker_bench(torch, hc, synth, npaths=456, cap=200, plain_sample=2):
     """Path steps/s and paths/s of the batched tracker (all paths in one persistent
     kernel, FP64 LU + DD refinement; secant, quadratic, and quadratic + learned step
     proposer) against the plain GPU tracker (all-DD elimination, secant, plain step
-    control, one path per launch), on the uneven-path family (n 10..64, 20..200
-    monomials per polynomial, k 2..8, exponents 1..3, seed 3) and on its regular
-    variant (a pure power and a constant per polynomial, so paths end at regular roots;
-    end points compared with the plain tracker's at 1e-28)."""
+    control, one path per launch).  Two families of npaths systems (456 = one wave of
+    three blocks on each of 152 SMs): the uneven-path family (n 10..64, 20..200
+    monomials per polynomial, k 2..8, exponents 1..3, seed 3), whose paths all diverge,
+    tracked for at most `cap` stages each (path steps/s); and its regular variant (a pure
+    power and a constant per polynomial, seed 33), tracked to the end (paths/s, end
+    points compared with the batched all-DD tracker's at 1e-28)."""
     import numpy as np
     prop = None
     if os.path.exists(PROPOSER):
@@ -217,7 +219,8 @@ def tracker_bench(torch, hc, synth, npaths=128, plain_sample=2):
         n = int(rng.integers(10, 65))
         reg.append((synth.regular_system(rng, n, (20, 200), (2, 8), (1, 3), lead=1),
                     synth.unit_complex(rng)))
-    fams = {"uneven": [synth.uneven_path_system(3, j) for j in range(npaths)], "uneven_regular": reg}
+    fams = {"uneven": ([synth.uneven_path_system(3, j) for j in range(npaths)], dict(max_steps=cap)),
+            "uneven_regular": (reg, {})}
     variants = [("batched_secant", dict(lu_mode=hc.HC_LU_FP64_REFINE)),
                 ("batched_quadratic", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC))]
     if prop is not None:
@@ -225,29 +228,34 @@ def tracker_bench(torch, hc, synth, npaths=128, plain_sample=2):
                          dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC,
                               proposer=prop.data_ptr())))
     out = {}
-    for name, fam in fams.items():
+    for name, (fam, extra) in fams.items():
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
-        plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE)
-        p_steps, p_dt, p_ends = 0, 0.0, []
+        plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE, **extra)
+        p_steps, p_dt = 0, 0.0
         for j in range(plain_sample):
-            pst, pends, pdt = run(systems[j:j + 1], gammas[j:j + 1], plain)
+            pst, _, pdt = run(systems[j:j + 1], gammas[j:j + 1], plain)
             p_steps += pst[0]["n_corr"]
             p_dt += pdt
-        ref_st, ref_ends, _ = run(systems, gammas, hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE))
-        res = {"paths": npaths, "plain_one_path_per_launch": {
-            "path_steps_per_s": p_steps / p_dt, "paths_per_s": plain_sample / p_dt,
-            "sample_paths": plain_sample}}
+        ref_st, ref_ends, ref_dt = run(systems, gammas, plain)
+        ref_steps = sum(x["n_corr"] for x in ref_st)
+        res = {"paths": npaths, "stage_cap": extra.get("max_steps"),
+               "plain_one_path_per_launch": {"path_steps_per_s": p_steps / p_dt,
+                                             "paths_per_s": plain_sample / p_dt,
+                                             "sample_paths": plain_sample},
+               "batched_all_dd_secant": {"path_steps_per_s": ref_steps / ref_dt,
+                                         "paths_per_s": npaths / ref_dt}}
         for vname, kw in variants:
-            st, ends, dt = run(systems, gammas, hc.hc_track_opts_default(**kw))
+            st, ends, dt = run(systems, gammas, hc.hc_track_opts_default(**kw, **extra))
             steps = sum(x["n_corr"] for x in st)
             same = sum(1 for p in range(npaths) if st[p]["status"] == hc.HC_OK and ref_st[p]["status"] == hc.HC_OK
                        and np.abs((ends[p] - ref_ends[p]).sum(-1)).max()
                        <= 1e-28 * max(1.0, np.abs(ref_ends[p].sum(-1)).max()))
             res[vname] = {"path_steps_per_s": steps / dt, "paths_per_s": npaths / dt,
+                          "speedup_steps_vs_plain": (steps / dt) / (p_steps / p_dt),
                           "speedup_paths_vs_plain": (npaths / dt) / (plain_sample / p_dt),
                           "mean_stages": steps / npaths,
                           "ok_paths": sum(1 for x in st if x["status"] == hc.HC_OK),
-                          "same_end_point_as_plain_1e-28": same,
+                          "same_end_point_as_batched_all_dd_1e-28": same,
                           "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
         out[name] = res
     return out

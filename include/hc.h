@@ -175,6 +175,13 @@ typedef struct {
                                 stage to [max(lambda_min, lambda_p / 4), lambda_max],
                                 after a rejection to at most shrink * the step that
                                 failed, and MIN_STEP when that is below lambda_min */
+    double explore;          /* for collecting the proposer's training data: the next step
+                                of the plain controller times 2^u, u uniform in
+                                [-explore, explore], clamped to [lambda_min, lambda_max];
+                                u from SplitMix64 (Steele, Lea & Flood 2014) of
+                                explore_seed ^ (path index << 32) ^ stage count.  0 (the
+                                default) = off; ignored with a proposer */
+    uint64_t explore_seed;
 } hc_track_opts;
 
 /* Per-path result (the statistics of Tables 2-3). */

@@ -36,7 +36,7 @@ struct GArgs {
     PathState *st;
     GStage *g;
     const double *x0;
-    double *z, *zp, *zpp, *zh, *ZP, *PW, *V, *H, *JH, *B, *RV, *DZ;
+    double *z, *zp, *zpp, *zh, *ZP, *PW, *V, *HS, *H, *JH, *B, *RV, *DZ;
     int32_t *PIV;
     hc_track_opts o;
     hc_step_record *log;
@@ -55,7 +55,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
     const int n = a.S.n, tid = threadIdx.x;
     if (st.phase == 0) {
         for (int q = tid; q < 2 * L * n; q += HC_TB) a.z[q] = a.x0[q];
-        path_init(st, a.o);
+        path_init(st, a.o, 0);
         __syncthreads();
         if (tid == 0) *a.st = st;
     }
@@ -91,8 +91,13 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
 
 template <int L> __global__ void __launch_bounds__(HC_TB) k_g_powers(GArgs a)
 {
-    if (!g_active(*a.g)) return;
-    for (int j = threadIdx.x; j < a.S.n; j += HC_TB) powers_of<L>(a.S, j, a.zh, a.PW);
+    const GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
+    for (int j = threadIdx.x; j < a.S.n; j += HC_TB) {
+        powers_of<L>(a.S, j, a.zh, a.PW);
+        homotopy_terms<L>(a.S, j, a.zh, gs, a.HS);
+    }
 }
 
 template <int L> __global__ void __launch_bounds__(HC_TB) k_g_monomials(GArgs a)
@@ -106,17 +111,17 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_entries(GArgs a)
 {
     const GStage &g = *a.g;
     if (!g_active(g)) return;
-    const int e = blockIdx.x * HC_TB + threadIdx.x;
+    const int q = blockIdx.x * HC_TB + threadIdx.x;
     const int ne = a.S.npoly * (a.S.n + 1);
-    if (e >= ne) return;
-    const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
-    entry_from_V<L>(a.S, e, a.zh, g.t1, gs, a.V, a.H, a.JH);
+    if (q >= ne) return;
+    entry_from_V<L>(a.S, __ldg(a.S.eperm + q), g.t1, a.V, a.HS, a.H, a.JH);
 }
 
 // residual of the incoming point, FP64 LU, first solve (block_newton's first half)
 template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a)
 {
     __shared__ BlockShared sh;
+    extern __shared__ double ysh[];  // [2][n]
     GStage &g = *a.g;
     if (!g_active(g)) return;
     const int n = a.S.n, tid = threadIdx.x;
@@ -141,10 +146,11 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a)
             a.RV[n + i] = -im;
         }
         __syncthreads();
-        block_lu64_solve(n, a.B, a.PIV, a.RV);
+        if (tid < 32) warp_lu64_solve(n, a.B, a.PIV, a.RV, ysh);
+        __syncthreads();
         double xn = 0.0;
         for (int i = tid; i < n; i += HC_TB) {
-            st_c<L>(a.DZ, n, i, c_from<L>(a.RV[i], a.RV[n + i]));
+            st_c<L>(a.DZ, n, i, c_from<L>(ysh[i], ysh[n + i]));
             double re, im;
             ld_lead<L>(a.zh, n, i, re, im);
             xn = fmax(xn, sqrt(add_(mul_(re, re), mul_(im, im))));
@@ -198,20 +204,21 @@ template <int L> __global__ void __launch_bounds__(32) k_g_refine_rows(GArgs a)
 template <int L> __global__ void __launch_bounds__(HC_TB) k_g_refine_solve(GArgs a)
 {
     __shared__ BlockShared sh;
+    extern __shared__ double ysh[];  // [2][n]
     GStage &g = *a.g;
     if (!g_active(g) || !g.refine_active) return;
     const int n = a.S.n, tid = threadIdx.x;
-    block_lu64_solve(n, a.B, a.PIV, a.RV);
+    if (tid < 32) warp_lu64_solve(n, a.B, a.PIV, a.RV, ysh);
+    __syncthreads();
     double dn = 0.0, zz = 0.0;
     for (int i = tid; i < n; i += HC_TB) {
-        const double dr = a.RV[i], di = a.RV[n + i];
+        const double dr = ysh[i], di = ysh[n + i];
         const C<L> v = c_add(ld_c<L>(a.DZ, n, i), c_from<L>(dr, di));
         st_c<L>(a.DZ, n, i, v);
         dn = fmax(dn, sqrt(add_(mul_(dr, dr), mul_(di, di))));
         zz = fmax(zz, sqrt(c_abs2_lead(v)));
     }
-    dn = block_max(dn, sh);
-    zz = block_max(zz, sh);
+    block_max2(dn, zz, sh);
     if (tid == 0) {
         g.sweeps++;
         const double tol = ldexp(1.0, -53 * L);
@@ -287,6 +294,7 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
 {
     const int mblocks = (a.S.nmon + HC_TB - 1) / HC_TB;
     const int eblocks = (a.S.npoly * (a.S.n + 1) + HC_TB - 1) / HC_TB;
+    const size_t ysh_bytes = sizeof(double) * 2 * (size_t)a.S.n;  // n <= 256: at most 4 KiB
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return hc_cuda_fail(e, "cudaStreamBeginCapture");
@@ -295,10 +303,10 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
         k_g_powers<L><<<1, HC_TB, 0, cs>>>(a);
         k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_TB, 0, cs>>>(a);
         k_g_entries<L><<<eblocks, HC_TB, 0, cs>>>(a);
-        k_g_factor<L><<<1, HC_TB, 0, cs>>>(a);
+        k_g_factor<L><<<1, HC_TB, ysh_bytes, cs>>>(a);
         for (int r = 0; r < max_refine; r++) {
             k_g_refine_rows<L><<<a.S.n, 32, 0, cs>>>(a);
-            k_g_refine_solve<L><<<1, HC_TB, 0, cs>>>(a);
+            k_g_refine_solve<L><<<1, HC_TB, ysh_bytes, cs>>>(a);
         }
         k_g_update<L><<<1, HC_TB, 0, cs>>>(a);
     }
@@ -327,7 +335,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     const size_t o_zp = put(vec), o_zpp = put(vec), o_zh = put(vec), o_ZP = put(vec);
     const size_t o_pw = put(vec * (s->max_exp > 2 ? s->max_exp - 2 : 1));
     const size_t o_v = put(sizeof(double) * 2 * L * (vplane > 0 ? vplane : 1));
-    const size_t o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n);
+    const size_t o_hs = put(2 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n);
     const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n);
     void *ws = nullptr;
     HC_CUDA_TRY(cudaMalloc(&ws, off));
@@ -344,6 +352,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     a.ZP = (double *)(b + o_ZP);
     a.PW = (double *)(b + o_pw);
     a.V = (double *)(b + o_v);
+    a.HS = (double *)(b + o_hs);
     a.H = (double *)(b + o_h);
     a.JH = (double *)(b + o_jh);
     a.B = (double *)(b + o_b);

@@ -26,6 +26,8 @@ struct DevSys {
     const int32_t *tlist;     // [nvar+nmon] slot in V of each contribution: var_ptr[m]+q for
                               // the partial of monomial m in its q-th variable, nvar+m for
                               // its value; original monomial order within an entry
+    const int32_t *eperm;     // [npoly*(n+1)] entries by contribution count, descending (ties
+                              // by entry), so the lanes of a warp sum lists of equal length
 };
 
 struct hc_system {

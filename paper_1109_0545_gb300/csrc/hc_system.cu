@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "hc_internal.h"
@@ -205,6 +206,7 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (nmon > 0 ? nmon : 1));
     int32_t *tptr = (int32_t *)calloc((size_t)ne + 1, sizeof(int32_t));
     int32_t *tlist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nvar + nmon > 0 ? nvar + nmon : 1));
+    std::vector<int32_t> eperm((size_t)(ne > 0 ? ne : 1));
     if (!perm || !tptr || !tlist) {
         free(perm); free(tptr); free(tlist);
         hc_system_free(s);
@@ -241,9 +243,14 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
                     tlist[fill[i * (n + 1) + var_idx[q]]++] = q;
             }
         free(fill);
+        // entries by contribution count, longest first; the sort is stable
+        for (int q = 0; q < ne; q++) eperm[q] = q;
+        std::stable_sort(eperm.begin(), eperm.begin() + ne, [&](int32_t a, int32_t b) {
+            return tptr[a + 1] - tptr[a] > tptr[b + 1] - tptr[b];
+        });
     }
 
-    // one device block: mon_ptr | var_ptr | var_pack | deg | perm | tptr | tlist | coef
+    // one device block: mon_ptr | var_ptr | var_pack | deg | perm | tptr | tlist | eperm | coef
     size_t o_mon = 0;
     size_t o_var = hc_align256(o_mon + sizeof(int32_t) * (npoly + 1));
     size_t o_pack = hc_align256(o_var + sizeof(int32_t) * (nmon + 1));
@@ -251,7 +258,8 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     size_t o_perm = hc_align256(o_deg + sizeof(int32_t) * npoly);
     size_t o_tptr = hc_align256(o_perm + sizeof(int32_t) * (nmon > 0 ? nmon : 1));
     size_t o_tlist = hc_align256(o_tptr + sizeof(int32_t) * ((size_t)ne + 1));
-    size_t o_coef = hc_align256(o_tlist + sizeof(int32_t) * (size_t)(nvar + nmon > 0 ? nvar + nmon : 1));
+    size_t o_eperm = hc_align256(o_tlist + sizeof(int32_t) * (size_t)(nvar + nmon > 0 ? nvar + nmon : 1));
+    size_t o_coef = hc_align256(o_eperm + sizeof(int32_t) * (size_t)(ne > 0 ? ne : 1));
     size_t total = hc_align256(o_coef + sizeof(double) * 2 * prec * (size_t)(nmon > 0 ? nmon : 1));
     cudaError_t e = cudaMalloc(&s->dev_block, total);
     if (e != cudaSuccess) {
@@ -268,6 +276,8 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     if (e == cudaSuccess) e = cudaMemcpy(b + o_tptr, tptr, sizeof(int32_t) * ((size_t)ne + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nvar + nmon > 0)
         e = cudaMemcpy(b + o_tlist, tlist, sizeof(int32_t) * (size_t)(nvar + nmon), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ne > 0)
+        e = cudaMemcpy(b + o_eperm, eperm.data(), sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nmon > 0)
         e = cudaMemcpy(b + o_coef, coef, sizeof(double) * 2 * prec * (size_t)nmon, cudaMemcpyHostToDevice);
     free(perm);
@@ -290,6 +300,7 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     d.perm = (const int32_t *)(b + o_perm);
     d.tptr = (const int32_t *)(b + o_tptr);
     d.tlist = (const int32_t *)(b + o_tlist);
+    d.eperm = (const int32_t *)(b + o_eperm);
     d.coef = (const double *)(b + o_coef);
     d.gre = gamma[0];
     d.gim = gamma[1];

@@ -18,7 +18,7 @@
 namespace hc {
 
 struct SlotLayout {
-    size_t pw, v, h, jh, b, rv, dz, zp, piv, stride;
+    size_t pw, v, hs, h, jh, b, dz, zp, stride;
 };
 
 struct TrackArgs {
@@ -36,21 +36,32 @@ struct TrackArgs {
     hc_step_record *log;
     int log_cap;
     int npaths;
+    int nmax;                 // largest n of the batch
+    int b_smem;               // the FP64 factors in shared memory (else in the slot)
 };
 
-template <int L> __device__ __forceinline__ Slot<L> slot_of(const TrackArgs &a, int b)
+// Dynamic shared memory of a tracking block, in doubles: Y, RV [2][nmax] each, PIV
+// [nmax] ints, then (b_smem) the FP64 factors B [2][nmax][nmax].
+__host__ __device__ __forceinline__ size_t track_smem_doubles(int nmax, int b_smem)
+{
+    return 4 * (size_t)nmax + (size_t)(nmax + 1) / 2 + (b_smem ? 2 * (size_t)nmax * nmax : 0);
+}
+
+template <int L> __device__ __forceinline__ Slot<L> slot_of(const TrackArgs &a, int b, double *dsm)
 {
     char *base = a.slots + (size_t)b * a.lay.stride;
     Slot<L> w;
     w.PW = (double *)(base + a.lay.pw);
     w.V = (double *)(base + a.lay.v);
+    w.HS = (double *)(base + a.lay.hs);
     w.H = (double *)(base + a.lay.h);
     w.JH = (double *)(base + a.lay.jh);
-    w.B = (double *)(base + a.lay.b);
-    w.RV = (double *)(base + a.lay.rv);
     w.DZ = (double *)(base + a.lay.dz);
     w.ZP = (double *)(base + a.lay.zp);
-    w.PIV = (int32_t *)(base + a.lay.piv);
+    w.Y = dsm;
+    w.RV = dsm + 2 * a.nmax;
+    w.PIV = (int32_t *)(dsm + 4 * a.nmax);
+    w.B = a.b_smem ? dsm + 4 * (size_t)a.nmax + (a.nmax + 1) / 2 : (double *)(base + a.lay.b);
     return w;
 }
 
@@ -74,7 +85,7 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
     if (st.phase == 3) return;
     if (st.phase == 0) {
         for (int q = tid; q < 2 * L * n; q += HC_TB) z[q] = a.x0[a.xoff[p] + q];
-        path_init(st, o);
+        path_init(st, o, p);
         __syncthreads();
     }
     hc_step_record *log = a.log ? a.log + (size_t)p * a.log_cap : nullptr;
@@ -126,11 +137,12 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
 }
 
 template <int L>
-__global__ void __launch_bounds__(HC_TB) k_track(TrackArgs a, int persistent)
+__global__ void __launch_bounds__(HC_TB, 3) k_track(TrackArgs a, int persistent)
 {
     __shared__ BlockShared sh;
     __shared__ int s_p;
-    const Slot<L> w = slot_of<L>(a, blockIdx.x);
+    extern __shared__ double dsm[];
+    const Slot<L> w = slot_of<L>(a, blockIdx.x, dsm);
     if (persistent) {
         for (;;) {
             if (threadIdx.x == 0) s_p = atomicAdd(a.queue, 1);
@@ -177,6 +189,8 @@ extern "C" void hc_track_opts_default(hc_track_opts *o)
     o->graph_steps = 16;
     o->proposer = NULL;
     o->proposer_margin = 0.5;
+    o->explore = 0.0;
+    o->explore_seed = 0;
 }
 
 static int check_opts(const hc_track_opts *o)
@@ -202,20 +216,23 @@ static int check_opts(const hc_track_opts *o)
         return hc_fail(HC_EINVAL, "graph_steps out of [1, 1024]");
     if (o->proposer && !(o->proposer_margin >= 0.0 && o->proposer_margin < 64.0))
         return hc_fail(HC_EINVAL, "proposer_margin out of [0, 64)");
+    if (!(o->explore >= 0.0 && o->explore <= 8.0)) return hc_fail(HC_EINVAL, "explore out of [0, 8]");
     return HC_SUCCESS;
 }
 
 template <int L>
-static int launch_track(TrackArgs &a, int grid, int persistent, cudaStream_t st)
+static int launch_track(TrackArgs &a, int grid, int persistent, size_t smem, cudaStream_t st)
 {
-    k_track<L><<<grid, HC_TB, 0, st>>>(a, persistent);
+    k_track<L><<<grid, HC_TB, smem, st>>>(a, persistent);
     return HC_SUCCESS;
 }
 
-template <int L> static int occupancy_track()
+// blocks per SM at this dynamic shared memory size (which is opted into first)
+template <int L> static int occupancy_track(size_t smem)
 {
+    cudaFuncSetAttribute(k_track<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_track<L>, HC_TB, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_track<L>, HC_TB, smem);
     return occ < 1 ? 1 : occ;
 }
 
@@ -264,7 +281,11 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         return HC_SUCCESS;
     }
     const int sms = hc_num_sms();
-    int occ = L == 1 ? occupancy_track<1>() : L == 2 ? occupancy_track<2>() : occupancy_track<4>();
+    // the FP64 factors go to shared memory when a block's share stays within 72 KiB (three
+    // blocks per SM, the register limit, then still fit in the SM's 228 KiB)
+    const int b_smem = sizeof(double) * track_smem_doubles(nmax, 1) <= 72 * 1024;
+    const size_t smem = sizeof(double) * track_smem_doubles(nmax, b_smem);
+    int occ = L == 1 ? occupancy_track<1>(smem) : L == 2 ? occupancy_track<2>(smem) : occupancy_track<4>(smem);
     const int grid = (int)(npaths < (long long)sms * occ ? npaths : (long long)sms * occ);
 
     SlotLayout lay;
@@ -272,13 +293,12 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     auto put = [&](size_t bytes) { size_t at = o; o = hc_align256(o + bytes); return at; };
     lay.pw = put(sizeof(double) * 2 * L * (size_t)nmax * (emax > 2 ? emax - 2 : 1));
     lay.v = put(sizeof(double) * 2 * L * (size_t)(vmax > 0 ? vmax : 1));
+    lay.hs = put(sizeof(double) * 2 * L * 2 * (size_t)nmax);
     lay.h = put(sizeof(double) * 2 * L * (size_t)nmax);
     lay.jh = put(sizeof(double) * 2 * L * (size_t)nmax * nmax);
-    lay.b = put(sizeof(double) * 2 * (size_t)nmax * nmax);
-    lay.rv = put(sizeof(double) * 2 * (size_t)nmax);
+    lay.b = put(b_smem ? 0 : sizeof(double) * 2 * (size_t)nmax * nmax);
     lay.dz = put(sizeof(double) * 2 * L * (size_t)nmax);
     lay.zp = put(sizeof(double) * 2 * L * (size_t)nmax);
-    lay.piv = put(sizeof(int32_t) * (size_t)nmax);
     lay.stride = o;
 
     size_t b_sys = hc_align256(sizeof(DevSys) * npaths);
@@ -307,6 +327,8 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     a.log = log_cap > 0 ? log : nullptr;
     a.log_cap = log_cap;
     a.npaths = npaths;
+    a.nmax = nmax;
+    a.b_smem = b_smem;
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.sys, hs.data(), sizeof(DevSys) * npaths, cudaMemcpyHostToDevice, st));
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.xoff, off.data(), sizeof(long long) * npaths, cudaMemcpyHostToDevice, st));
     HC_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(PathState) * npaths, st));
@@ -314,9 +336,9 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     HC_CUDA_TRY(cudaMemcpyAsync(ctr, hctr, sizeof hctr, cudaMemcpyHostToDevice, st));
 
     if (opts->mode == HC_TRACK_PERSISTENT) {
-        if (L == 1) launch_track<1>(a, grid, 1, st);
-        else if (L == 2) launch_track<2>(a, grid, 1, st);
-        else launch_track<4>(a, grid, 1, st);
+        if (L == 1) launch_track<1>(a, grid, 1, smem, st);
+        else if (L == 2) launch_track<2>(a, grid, 1, smem, st);
+        else launch_track<4>(a, grid, 1, smem, st);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return hc_cuda_fail(e, "k_track launch");
     } else {
@@ -332,9 +354,9 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             for (int g = 0; g < opts->graph_steps; g++) {
-                if (L == 1) launch_track<1>(a, grid, 0, cs);
-                else if (L == 2) launch_track<2>(a, grid, 0, cs);
-                else launch_track<4>(a, grid, 0, cs);
+                if (L == 1) launch_track<1>(a, grid, 0, smem, cs);
+                else if (L == 2) launch_track<2>(a, grid, 0, smem, cs);
+                else launch_track<4>(a, grid, 0, smem, cs);
             }
             e = cudaStreamEndCapture(cs, &graph);
         }

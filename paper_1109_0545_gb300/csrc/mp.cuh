@@ -39,14 +39,17 @@ __device__ __forceinline__ void fast_two_sum(double a, double b, double &s, doub
     e = sub_(b, sub_(s, a));
 }
 
-// s + e = a + b exactly for any a, b: order the operands by magnitude, comparing the
-// bit patterns as integers (the INT pipe; GB300's FP64 pipe is ~40x scarcer), then
-// Dekker's fast two-sum.  3 FP64.
+// s + e = a + b exactly for any a, b: order the operands by exponent, then Dekker's fast
+// two-sum (exact whenever the first operand's exponent is not below the second's).  The
+// order comes from the high 32 bits of each operand shifted left by one (sign dropped:
+// exponent and leading fraction bits) compared as unsigned integers, all on the INT pipe.
+// (Clearing the sign bit with a mask instead is compiled as an FP64 absolute value, two
+// more FP64 instructions.)  3 FP64.
 __device__ __forceinline__ void two_sum_ord(double a, double b, double &s, double &e)
 {
-    const unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffULL;
-    const unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffULL;
-    const bool keep = ua >= ub;
+    const unsigned ha = (unsigned)__double2hiint(a) << 1;
+    const unsigned hb = (unsigned)__double2hiint(b) << 1;
+    const bool keep = ha >= hb;
     fast_two_sum(keep ? a : b, keep ? b : a, s, e);
 }
 
@@ -250,6 +253,15 @@ __device__ __forceinline__ R<4> r_div(R<4> a, R<4> b)
 }
 
 // ---------------------------------------------------------------- small integers
+// the double of an integer 1 <= k < 2^52 built from its bits (no FP64 conversion
+// instruction): exponent from the leading bit, the bits below it as the fraction
+__device__ __forceinline__ double int_to_double_exact(int k)
+{
+    const int e = 31 - __clz(k);
+    const unsigned long long frac = ((unsigned long long)k << (52 - e)) & 0xfffffffffffffULL;
+    return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | frac));
+}
+
 // a * k for a small positive integer k: exact for powers of two (exponent arithmetic,
 // no FP64 instruction), r_mul_d otherwise.
 template <int L> __device__ __forceinline__ R<L> r_scale_int(R<L> a, int k)
@@ -261,7 +273,7 @@ template <int L> __device__ __forceinline__ R<L> r_scale_int(R<L> a, int k)
         for (int j = 0; j < L; j++) a.v[j] = ldexp_exact(a.v[j], e);
         return a;
     }
-    return r_mul_d(a, (double)k);
+    return r_mul_d(a, int_to_double_exact(k));
 }
 
 // ---------------------------------------------------------------- complex

@@ -9,21 +9,26 @@ namespace hc {
 #define HC_TB 128          // threads per path block
 #define HC_TW (HC_TB / 32)
 
-// per-slot scratch of one block (global memory, sized for the largest system)
+// per-slot scratch of one block (global memory sized for the largest system; the solve's
+// vectors, and the FP64 factors where they fit, in shared memory)
 template <int L> struct Slot {
     double *PW;    // [max_exp-2][2][L][n]
     double *V;     // [2][L][nvar+nmon] (plane = nvar+nmon): partials, then values
+    double *HS;    // [2][L][2n] start-system terms of the homotopy per row: gamma (1-t)
+                   // (x_i^d_i - 1), then gamma (1-t) d_i x_i^(d_i - 1)
     double *H;     // [2][L][n]
     double *JH;    // [2][L][n][n]
     double *B;     // [2][n][n] FP64 factors
-    double *RV;    // [2][n]
+    double *RV;    // [2][n] right-hand side of an FP64 solve
+    double *Y;     // [2][n] solution of an FP64 solve
     double *DZ;    // [2][L][n]
     double *ZP;    // [2][L][n] the predicted point of the current stage
-    int32_t *PIV;  // [n]
+    int32_t *PIV;  // [n] row permutation of the factors
 };
 
 struct BlockShared {
     double rv[HC_TW];
+    double rv2[HC_TW];
     int ri[HC_TW];
     double bc[4];
     int ibc[4];
@@ -47,6 +52,26 @@ __device__ __forceinline__ double block_max(double v, BlockShared &sh)
 #pragma unroll
     for (int w = 1; w < HC_TW; w++) m = fmax(m, sh.rv[w]);
     return m;
+}
+
+// two maxima over the block with one pair of barriers
+__device__ __forceinline__ void block_max2(double &a, double &b, BlockShared &sh)
+{
+    a = warp_max(a);
+    b = warp_max(b);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        sh.rv[threadIdx.x >> 5] = a;
+        sh.rv2[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    a = sh.rv[0];
+    b = sh.rv2[0];
+#pragma unroll
+    for (int w = 1; w < HC_TW; w++) {
+        a = fmax(a, sh.rv[w]);
+        b = fmax(b, sh.rv2[w]);
+    }
 }
 
 __device__ __forceinline__ int block_and(int v, BlockShared &sh)
@@ -143,12 +168,27 @@ __device__ __forceinline__ void powers_of(const DevSys &S, int j, const double *
     }
 }
 
+// Start-system terms of row i of the homotopy at (z, t), t >= 0: gamma (1-t) (x_i^d - 1)
+// into HS[i] and gamma (1-t) d x_i^(d-1) into HS[n + i] (d = deg f_i), gs = gamma (1-t).
+template <int L>
+__device__ __forceinline__ void homotopy_terms(const DevSys &S, int i, const double *__restrict__ z,
+                                               const C<L> &gs, double *__restrict__ HS)
+{
+    const int n = S.n, d = __ldg(S.deg + i);
+    const C<L> xi = ld_c<L>(z, n, i);
+    const C<L> xd1 = c_pow(xi, d - 1);
+    C<L> g = c_mul(xd1, xi);
+    g.re = r_sub(g.re, r_from<L>(1.0));
+    st_c<L>(HS, 2 * n, i, c_mul(gs, g));
+    st_c<L>(HS, 2 * n, n + i, c_mul(gs, c_scale_int(xd1, d)));
+}
+
 // Phase 2 for one entry e = i (n+1) + j: the sum of its contributions in the original
 // monomial order, then the homotopy (t >= 0); j == n is h_i, else dh_i/dx_j.
 template <int L>
-__device__ __forceinline__ void entry_from_V(const DevSys &S, int e, const double *__restrict__ z, double t,
-                                             const C<L> &gs, const double *__restrict__ V,
-                                             double *__restrict__ H, double *__restrict__ JH)
+__device__ __forceinline__ void entry_from_V(const DevSys &S, int e, double t, const double *__restrict__ V,
+                                             const double *__restrict__ HS, double *__restrict__ H,
+                                             double *__restrict__ JH)
 {
     const int n = S.n;
     const size_t vplane = (size_t)S.nvar + S.nmon;
@@ -160,15 +200,11 @@ __device__ __forceinline__ void entry_from_V(const DevSys &S, int e, const doubl
 #pragma unroll 4
     for (int r = __ldg(S.tptr + e); r < r1; r++) acc = c_add(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
     if (t >= 0.0) {
-        const int d = __ldg(S.deg + i);
-        const C<L> xi = ld_c<L>(z, n, i);
         if (j == n) {
-            C<L> g = c_mul(c_pow(xi, d - 1), xi);
-            g.re = r_sub(g.re, r_from<L>(1.0));
-            acc = c_add(c_mul(gs, g), c_mul_d(acc, t));
+            acc = c_add(ld_c<L>(HS, 2 * n, i), c_mul_d(acc, t));
         } else {
             acc = c_mul_d(acc, t);
-            if (i == j) acc = c_add(acc, c_mul(gs, c_scale_int(c_pow(xi, d - 1), d)));
+            if (i == j) acc = c_add(acc, ld_c<L>(HS, 2 * n, n + i));
         }
     }
     if (j == n)
@@ -177,17 +213,22 @@ __device__ __forceinline__ void entry_from_V(const DevSys &S, int e, const doubl
         st_c<L>(JH, (size_t)n * n, (size_t)i * n + j, acc);
 }
 
+// h(z, t) (or f(z) for t < 0) and its Jacobian by the block; entries are taken in the
+// order of S.eperm (longest contribution lists first)
 template <int L>
 __device__ void block_eval(const DevSys &S, const double *__restrict__ z, double t, const Slot<L> &w)
 {
     const int n = S.n, tid = threadIdx.x;
-    for (int j = tid; j < n; j += HC_TB) powers_of<L>(S, j, z, w.PW);
+    const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
+    for (int j = tid; j < n; j += HC_TB) {
+        powers_of<L>(S, j, z, w.PW);
+        if (t >= 0.0 && j < S.npoly) homotopy_terms<L>(S, j, z, gs, w.HS);
+    }
     __syncthreads();
     for (int q = tid; q < S.nmon; q += HC_TB) monomial_to_V<L>(S, __ldg(S.perm + q), z, w.PW, w.V);
     __syncthreads();
-    const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
     const int ne = S.npoly * (n + 1);
-    for (int e = tid; e < ne; e += HC_TB) entry_from_V<L>(S, e, z, t, gs, w.V, w.H, w.JH);
+    for (int q = tid; q < ne; q += HC_TB) entry_from_V<L>(S, __ldg(S.eperm + q), t, w.V, w.HS, w.H, w.JH);
     __syncthreads();
 }
 
@@ -270,7 +311,8 @@ __device__ __forceinline__ cdv cdv_fnma(cdv acc, cdv a, cdv b)
 }
 
 // FP64 LU of the leading limbs with partial pivoting (the same pivot rule), block version.
-// B[2][n][n] gets L (unit, below the diagonal), U, and the reciprocals of U's diagonal.
+// B[2][n][n] gets L (unit, below the diagonal), U, and the reciprocals of U's diagonal;
+// PIV[k] is the original row that ends in row k (the row swaps composed).
 template <int L>
 __device__ int block_lu64(int n, const double *__restrict__ A, double *__restrict__ B, int32_t *__restrict__ PIV,
                           BlockShared &sh, double *cond)
@@ -283,6 +325,7 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
         B[q] = re;
         B[ap + q] = im;
     }
+    for (int q = tid; q < n; q += HC_TB) PIV[q] = q;
     __syncthreads();
     auto ld = [&](int i, int j) { return cdv{B[(size_t)i * n + j], B[ap + (size_t)i * n + j]}; };
     auto st = [&](int i, int j, cdv v) { B[(size_t)i * n + j] = v.re; B[ap + (size_t)i * n + j] = v.im; };
@@ -303,13 +346,18 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
         pmax = fmax(pmax, bv);
         pmin = fmin(pmin, bv);
         const int piv = bi;
-        if (tid == 0) PIV[k] = piv;
-        if (piv != k)
+        if (piv != k) {
+            if (tid == 0) {
+                const int t0 = PIV[k];
+                PIV[k] = PIV[piv];
+                PIV[piv] = t0;
+            }
             for (int j = tid; j < n; j += HC_TB) {
                 const cdv t0 = ld(k, j);
                 st(k, j, ld(piv, j));
                 st(piv, j, t0);
             }
+        }
         __syncthreads();
         const cdv a = ld(k, k);
         const cdv inv = {a.re / bv, -a.im / bv};
@@ -327,47 +375,75 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
     return HC_OK;
 }
 
-// solve with the FP64 LU: RV[2][n] in place
-static __device__ void block_lu64_solve(int n, const double *__restrict__ B, const int32_t *__restrict__ PIV,
-                                 double *__restrict__ RV)
+// y = A^-1 r with the FP64 factors of block_lu64, by one warp (the calling warp): r[2][n]
+// in the original row order is permuted into y, then forward and back substitution with
+// warp barriers only.  y must not alias r.  The caller synchronises the block before
+// other warps read y.
+__device__ __forceinline__ void warp_lu64_solve(int n, const double *__restrict__ B, const int32_t *__restrict__ PIV,
+                                                const double *__restrict__ r, double *__restrict__ y)
 {
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const size_t ap = (size_t)n * n;
-    if (tid == 0)
-        for (int k = 0; k < n; k++) {
-            const int p = PIV[k];
-            if (p != k) {
-                double t0 = RV[k], t1 = RV[n + k];
-                RV[k] = RV[p];
-                RV[n + k] = RV[n + p];
-                RV[p] = t0;
-                RV[n + p] = t1;
-            }
-        }
-    __syncthreads();
+    for (int i = lane; i < n; i += 32) {
+        const int p = PIV[i];
+        y[i] = r[p];
+        y[n + i] = r[n + p];
+    }
+    __syncwarp();
     for (int k = 0; k < n - 1; k++) {
-        const cdv rk = {RV[k], RV[n + k]};
-        for (int i = k + 1 + tid; i < n; i += HC_TB) {
-            const cdv v = cdv_fnma(cdv{RV[i], RV[n + i]}, cdv{B[(size_t)i * n + k], B[ap + (size_t)i * n + k]}, rk);
-            RV[i] = v.re;
-            RV[n + i] = v.im;
+        const cdv yk = {y[k], y[n + k]};
+        for (int i = k + 1 + lane; i < n; i += 32) {
+            const cdv v = cdv_fnma(cdv{y[i], y[n + i]}, cdv{B[(size_t)i * n + k], B[ap + (size_t)i * n + k]}, yk);
+            y[i] = v.re;
+            y[n + i] = v.im;
         }
-        __syncthreads();
+        __syncwarp();
     }
     for (int i = n - 1; i >= 0; i--) {
-        if (tid == 0) {
-            const cdv v = cdv_mul(cdv{RV[i], RV[n + i]}, cdv{B[(size_t)i * n + i], B[ap + (size_t)i * n + i]});
-            RV[i] = v.re;
-            RV[n + i] = v.im;
+        const cdv zi = cdv_mul(cdv{y[i], y[n + i]}, cdv{B[(size_t)i * n + i], B[ap + (size_t)i * n + i]});
+        __syncwarp();
+        if (lane == 0) {
+            y[i] = zi.re;
+            y[n + i] = zi.im;
         }
-        __syncthreads();
-        const cdv zi = {RV[i], RV[n + i]};
-        for (int r = tid; r < i; r += HC_TB) {
-            const cdv v = cdv_fnma(cdv{RV[r], RV[n + r]}, cdv{B[(size_t)r * n + i], B[ap + (size_t)r * n + i]}, zi);
-            RV[r] = v.re;
-            RV[n + r] = v.im;
+        for (int q = lane; q < i; q += 32) {
+            const cdv v = cdv_fnma(cdv{y[q], y[n + q]}, cdv{B[(size_t)q * n + i], B[ap + (size_t)q * n + i]}, zi);
+            y[q] = v.re;
+            y[n + q] = v.im;
         }
-        __syncthreads();
+        __syncwarp();
+    }
+}
+
+// r_i = -h_i - sum_j J_ij dz_j in L limbs, leading limbs into RV: T threads per row (the
+// largest power of two with T n <= the block), each summing a strided part of the row,
+// then a fixed shuffle tree adds the T parts
+template <int L>
+__device__ __forceinline__ void block_refine_residual(int n, const double *__restrict__ JH, const double *__restrict__ H,
+                                                      const double *__restrict__ DZ, double *__restrict__ RV)
+{
+    const int T = 8 * n <= HC_TB ? 8 : 4 * n <= HC_TB ? 4 : 2 * n <= HC_TB ? 2 : 1;
+    const int g = threadIdx.x / T, q = threadIdx.x % T, rows = HC_TB / T;
+    for (int base = 0; base < n; base += rows) {
+        const int i = base + g;
+        C<L> acc = c_zero<L>();
+        if (i < n)
+            for (int j = q; j < n; j += T)
+                acc = c_fnma(acc, ld_c<L>(JH, (size_t)n * n, (size_t)i * n + j), ld_c<L>(DZ, n, j));
+        for (int o = T >> 1; o > 0; o >>= 1) {
+            C<L> other;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                other.re.v[l] = __shfl_xor_sync(0xffffffffu, acc.re.v[l], o);
+                other.im.v[l] = __shfl_xor_sync(0xffffffffu, acc.im.v[l], o);
+            }
+            acc = c_add(acc, other);
+        }
+        if (i < n && q == 0) {
+            const C<L> r = c_sub(acc, ld_c<L>(H, n, i));
+            RV[i] = r.re.v[0];
+            RV[n + i] = r.im.v[0];
+        }
     }
 }
 
@@ -420,10 +496,11 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
             w.RV[n + i] = -im;
         }
         __syncthreads();
-        block_lu64_solve(n, w.B, w.PIV, w.RV);
+        if (tid < 32) warp_lu64_solve(n, w.B, w.PIV, w.RV, w.Y);
+        __syncthreads();
         double xn = 0.0;
         for (int i = tid; i < n; i += HC_TB) {
-            st_c<L>(w.DZ, n, i, c_from<L>(w.RV[i], w.RV[n + i]));
+            st_c<L>(w.DZ, n, i, c_from<L>(w.Y[i], w.Y[n + i]));
             double re, im;
             ld_lead<L>(z, n, i, re, im);
             xn = fmax(xn, sqrt(add_(mul_(re, re), mul_(im, im))));
@@ -432,27 +509,19 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
         const double tol = ldexp(1.0, -53 * L);
         double prev = INFINITY;
         for (int it = 1; it <= max_refine; it++) {
-            for (int i = tid; i < n; i += HC_TB) {
-                C<L> acc = ld_c<L>(w.H, n, i);
-                acc.re = r_neg(acc.re);
-                acc.im = r_neg(acc.im);
-                for (int j = 0; j < n; j++)
-                    acc = c_fnma(acc, ld_c<L>(w.JH, (size_t)n * n, (size_t)i * n + j), ld_c<L>(w.DZ, n, j));
-                w.RV[i] = acc.re.v[0];
-                w.RV[n + i] = acc.im.v[0];
-            }
+            block_refine_residual<L>(n, w.JH, w.H, w.DZ, w.RV);
             __syncthreads();
-            block_lu64_solve(n, w.B, w.PIV, w.RV);
+            if (tid < 32) warp_lu64_solve(n, w.B, w.PIV, w.RV, w.Y);
+            __syncthreads();
             double dn = 0.0, zz = 0.0;
             for (int i = tid; i < n; i += HC_TB) {
-                const double dr = w.RV[i], di = w.RV[n + i];
+                const double dr = w.Y[i], di = w.Y[n + i];
                 const C<L> v = c_add(ld_c<L>(w.DZ, n, i), c_from<L>(dr, di));
                 st_c<L>(w.DZ, n, i, v);
                 dn = fmax(dn, sqrt(add_(mul_(dr, dr), mul_(di, di))));
                 zz = fmax(zz, sqrt(c_abs2_lead(v)));
             }
-            dn = block_max(dn, sh);
-            zz = block_max(zz, sh);
+            block_max2(dn, zz, sh);
             o.sweeps = it;
             if (dn <= tol * fmax(xn, zz) || dn >= prev) break;
             prev = dn;
@@ -471,8 +540,9 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
         zn = fmax(zn, sqrt(c_abs2_lead(v)));
     }
     ok = block_and(ok, sh);
-    o.dzn = block_max(dzn, sh);
-    o.zn = block_max(zn, sh);
+    block_max2(dzn, zn, sh);
+    o.dzn = dzn;
+    o.zn = zn;
     if (!ok) {
         o.status = HC_NONFINITE;
         return o;

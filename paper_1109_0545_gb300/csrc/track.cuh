@@ -17,7 +17,17 @@ struct PathState {
     double hl[3], hr[3], pcd, cond;
     int hi[3], pad3;
     double lam_plain;  // the plain controller's step, run alongside the proposer
+    long long pid;     // path index (the exploration generator's stream)
 };
+
+// SplitMix64 (Steele, Lea & Flood 2014): one output of the generator at counter x
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    x += 0x9e3779b97f4a7c15ULL;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+    return x ^ (x >> 31);
+}
 
 // Features of the step proposer before the next stage, each scaled to order one:
 //   0      t
@@ -50,8 +60,9 @@ template <int L> __device__ __forceinline__ double vec_norm(int n, const double 
     return block_max(m, sh);
 }
 
-__device__ __forceinline__ void path_init(PathState &st, const hc_track_opts &o)
+__device__ __forceinline__ void path_init(PathState &st, const hc_track_opts &o, long long pid)
 {
+    st.pid = pid;
     st.t = st.tp = st.tpp = 0.0;
     st.lambda = o.lambda0;
     st.minstep = INFINITY;
@@ -221,6 +232,14 @@ __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared 
                     st.status = HC_MIN_STEP;
                 }
             }
+        }
+        // exploration for training data: the next step times 2^u, u uniform in
+        // [-explore, explore] (same value on every thread)
+        if (o.explore > 0.0 && !o.proposer && !stop) {
+            const unsigned long long r = splitmix64(o.explore_seed ^ ((unsigned long long)st.pid << 32) ^
+                                                    (unsigned long long)st.n_corr);
+            const double u = (double)(r >> 11) * 0x1.0p-53;
+            st.lambda = fmin(fmax(st.lambda * exp2(o.explore * (2.0 * u - 1.0)), o.lambda_min), o.lambda_max);
         }
         if (!stop && st.t < 1.0 && st.n_corr >= o.max_steps) {
             stop = 1;

@@ -38,7 +38,8 @@ class TrackOpts(ct.Structure):
                 ("max_it", ct.c_int32), ("end_it", ct.c_int32), ("grow_after", ct.c_int32),
                 ("max_steps", ct.c_int32), ("predictor", ct.c_int32), ("lu_mode", ct.c_int32),
                 ("max_refine", ct.c_int32), ("mode", ct.c_int32), ("graph_steps", ct.c_int32),
-                ("reserved", ct.c_int32), ("proposer", ct.c_void_p), ("proposer_margin", ct.c_double)]
+                ("reserved", ct.c_int32), ("proposer", ct.c_void_p), ("proposer_margin", ct.c_double),
+                ("explore", ct.c_double), ("explore_seed", ct.c_uint64)]
 
 
 class PathStats(ct.Structure):

@@ -165,10 +165,15 @@ def main():
     ap.add_argument("--weights", default="proposer_weights.npy")
     ap.add_argument("--uneven-eval-paths", type=int, default=512)
     ap.add_argument("--margins", default="0.5")
+    ap.add_argument("--explore", type=float, default=1.5,
+                    help="log2 range of the random step perturbation while collecting")
     args = ap.parse_args()
     import torch
     hc.load(build_if_missing=False)
-    plain = hc.hc_track_opts_default()
+    # the plain controller with its steps perturbed by 2^u, u uniform in
+    # [-explore, explore], so that the logs hold accepted and rejected steps over a range
+    # of ratios around the plain choice
+    plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, explore=args.explore)
     t0 = time.perf_counter()
     Xs, rs, as_ = [], [], []
     total, j = 0, 0
@@ -186,6 +191,7 @@ def main():
             for s, g in regular_family(1000 * seed + j, 16):
                 systems.append(s)
                 gammas.append(g)
+        plain.explore_seed = 1 + j
         j += 16
         X, r, a = collect(torch, systems, gammas, plain)
         Xs.append(X)
@@ -202,7 +208,8 @@ def main():
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     np.save(args.weights, params.cpu().numpy())
-    res = {"records": int(X.shape[0]), "accept_rate": float(a.mean()), "collect_s": t_collect,
+    res = {"records": int(X.shape[0]), "explore": args.explore, "accept_rate": float(a.mean()),
+           "collect_s": t_collect,
            "train_s": t_train, "train_steps": args.steps, "loss_first": losses[0],
            "loss_last": losses[-1]}
     margins = [float(v) for v in args.margins.split(",")]

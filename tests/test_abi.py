@@ -113,3 +113,39 @@ def test_layout_round_trip():
     assert soa.shape == (2, 2, 5, 3, 7)
     assert soa[1, 0, 4, 2, 6] == limbs[6, 4, 2, 1, 0]
     assert np.array_equal(hc.from_soa(soa), limbs)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the option, statistics and log structs have the sizes and
+    field offsets that a C compiler gives the declarations in include/hc.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"hc_track_opts": hc.TrackOpts, "hc_path_stats": hc.PathStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hc.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('printf("hc_step_record size %zu\\n", sizeof(hc_step_record));')
+    for fname, cfield in (("t", "t"), ("lam", "lambda"), ("res_first", "res_first"), ("res_last", "res_last"),
+                          ("pc_dist", "pc_dist"), ("cond_log10", "cond_log10"), ("iters", "iters"),
+                          ("accepted", "accepted")):
+        lines.append(f'printf("hc_step_record {fname} %zu\\n", offsetof(hc_step_record, {cfield}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ct.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+    rec = hc.STEP_RECORD_DTYPE
+    assert got[("hc_step_record", "size")] == rec.itemsize
+    for fname in rec.names:
+        assert got[("hc_step_record", fname)] == rec.fields[fname][1], fname

@@ -166,3 +166,39 @@ def test_uneven_family_end_points_are_roots():
         xn, _, stn, _ = oracle.newton_step(s.as_dict(), s.coef_limbs(2), x[None], -1.0, ga, 0)
         assert stn[0] == 0
         assert rel_err_per_point(xn, x[None])[0] < 1e-25
+
+
+def test_exploration_perturbs_steps_reproducibly_and_the_oracle_replays_them():
+    """explore = 0 is the plain tracker bit for bit; explore > 0 draws step ratios off the
+    plain controller's powers of two, the same ones for the same seed, and the oracle
+    following the accepted t sequence reaches the same end points."""
+    torch = torch_cuda()
+    fam = regular_family(470, 4, 3)
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    base = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE)
+    st0, ends0, _ = gpu_track(torch, systems, gammas, 2, base)
+    off = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, explore=0.0, explore_seed=99)
+    st1, ends1, _ = gpu_track(torch, systems, gammas, 2, off)
+    for a, b, x, y in zip(st0, st1, ends0, ends1):
+        assert (a["n_succ"], a["n_corr"], a["status"]) == (b["n_succ"], b["n_corr"], b["status"])
+        assert np.array_equal(x, y)
+    o = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, explore=1.5, explore_seed=7)
+    st, ends, recs = gpu_track(torch, systems, gammas, 2, o, log_cap=4000)
+    st2, ends2, recs2 = gpu_track(torch, systems, gammas, 2, o, log_cap=4000)
+    oo = oracle_opts(o)
+    off_lattice = 0
+    for p, (s, g) in enumerate(fam):
+        lg = recs[p][:st[p]["n_corr"]]
+        assert np.array_equal(lg, recs2[p][:st2[p]["n_corr"]])
+        ratios = np.log2(lg["lam"][1:-1] / lg["lam"][:-2])
+        off_lattice += int(np.sum(np.abs(ratios - np.round(ratios)) > 1e-9))
+        assert np.all(lg["lam"] <= o.lambda_max * (1 + 1e-15))
+        if st[p]["status"] != hc.HC_OK:
+            continue
+        acc = np.nonzero(lg["accepted"] == 1)[0]
+        tseq = [lg["t"][k + 1] if k + 1 < len(lg) else 1.0 for k in acc]
+        x1, status, fail = oracle.track_replay(s.as_dict(), s.coef_limbs(2), synth.limbs(np.ones(s.n), 2),
+                                               np.array([g.real, g.imag]), oo, tseq)
+        assert fail == -1 and status == 0
+        assert rel_err_per_point(ends[p][None], x1[None])[0] <= TOL[2]
+    assert off_lattice > 0
