@@ -185,7 +185,7 @@ def captured_traffic(npts: int):
 PROPOSER = os.path.join(ROOT, "paper_1109_0545_gb300", "data", "proposer_weights.npy")
 
 
-def tracker_bench(torch, hc, synth, npaths=456, cap=200, plain_sample=2):
+def tracker_bench(torch, hc, synth, peak_gops=None, npaths=456, cap=200, plain_sample=2):
     """Path steps/s and paths/s of the batched tracker (all paths in one persistent
     kernel, FP64 LU + DD refinement; secant, quadratic, and quadratic + learned step
     proposer) against the plain GPU tracker (all-DD elimination, secant, plain step
@@ -194,8 +194,12 @@ def tracker_bench(torch, hc, synth, npaths=456, cap=200, plain_sample=2):
     monomials per polynomial, k 2..8, exponents 1..3, seed 3), whose paths all diverge,
     tracked for at most `cap` stages each (path steps/s); and its regular variant (a pure
     power and a constant per polynomial, seed 33), tracked to the end (paths/s, end
-    points compared with the batched all-DD tracker's at 1e-28)."""
+    points compared with the batched all-DD tracker's at 1e-28).  FP64 throughput: the
+    Newton iterations of all paths (end game included) times the FP64 instructions of one
+    iteration without its refinement sweeps (`opcount.newton_iteration_ops`, a lower bound)
+    per second, against the measured FP64 peak."""
     import numpy as np
+    from paper_1109_0545_gb300 import opcount
     prop = None
     if os.path.exists(PROPOSER):
         prop = torch.from_numpy(np.load(PROPOSER).astype(np.float32)).cuda()
@@ -230,6 +234,7 @@ def tracker_bench(torch, hc, synth, npaths=456, cap=200, plain_sample=2):
     out = {}
     for name, (fam, extra) in fams.items():
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+        it_ops = [opcount.newton_iteration_ops(sy, 2) for sy in systems]
         plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE, **extra)
         p_steps, p_dt = 0, 0.0
         for j in range(plain_sample):
@@ -250,7 +255,10 @@ def tracker_bench(torch, hc, synth, npaths=456, cap=200, plain_sample=2):
             same = sum(1 for p in range(npaths) if st[p]["status"] == hc.HC_OK and ref_st[p]["status"] == hc.HC_OK
                        and np.abs((ends[p] - ref_ends[p]).sum(-1)).max()
                        <= 1e-28 * max(1.0, np.abs(ref_ends[p].sum(-1)).max()))
+            gops = sum((x["newton_its"] + x["end_its"]) * w for x, w in zip(st, it_ops)) / dt / 1e9
             res[vname] = {"path_steps_per_s": steps / dt, "paths_per_s": npaths / dt,
+                          "fp64_gops_at_least": gops,
+                          "fp64_frac_of_measured_peak_at_least": gops / peak_gops if peak_gops else None,
                           "speedup_steps_vs_plain": (steps / dt) / (p_steps / p_dt),
                           "speedup_paths_vs_plain": (npaths / dt) / (plain_sample / p_dt),
                           "mean_stages": steps / npaths,
@@ -258,6 +266,107 @@ def tracker_bench(torch, hc, synth, npaths=456, cap=200, plain_sample=2):
                           "same_end_point_as_batched_all_dd_1e-28": same,
                           "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
         out[name] = res
+    return out
+
+
+def paper_tables_bench(torch, hc, synth):
+    """One-path runs in complex QD (the paper's precision) on the shapes of its one-path
+    experiments, regular variant (a constant and x_i^(D+1) added per polynomial so that the
+    path ends at a root).  Table 4: n = 40, 40 monomials of degree 2 per polynomial, and of
+    degree 20; quadratic predictor; on one 128-thread block and on the whole GPU
+    (HC_TRACK_GRID); the paper's times on 8 cores of a 2011 Xeon are context.  Tables 2-3:
+    n = 20, 20 monomials of degree 10 per polynomial, three systems tracked together,
+    secant against quadratic predictor: successful / total corrector stages, average and
+    minimal accepted step, time."""
+    import numpy as np
+
+    def run(systems, gammas, **kw):
+        handles = [hc.system_from(s, 4, g) for s, g in zip(systems, gammas)]
+        x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 4) for s in systems])).cuda()
+        x1 = torch.zeros_like(x0)
+        o = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, eps=1e-58, eps_end=1e-58,
+                                     eps_end_x=1e-58, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = hc.hc_track_path(handles, x0, x1, o)
+        dt = time.perf_counter() - t0
+        for h in handles:
+            h.free()
+        return st, dt
+
+    def summary(st, dt):
+        return {"seconds": dt, "status": [hc.STATUS_NAMES[x["status"]] for x in st],
+                "succ_corrs": [int(x["n_succ"]) for x in st], "corrs": [int(x["n_corr"]) for x in st],
+                "avg_step": [x["avg_step"] for x in st], "min_step": [x["min_step"] for x in st],
+                "newton_its": [int(x["newton_its"]) for x in st],
+                "stages_per_s": sum(x["n_corr"] for x in st) / dt}
+
+    out = {}
+    paper_s = {2: 62.257, 20: 1942.671}
+    for deg in (2, 20):
+        s, g = synth.paper_dim_degree(40, 40, 40, deg)
+        r = {"n": 40, "monomials": s.nmon, "degree": deg, "paper_8_cores_s": paper_s[deg]}
+        for eng, mode in (("one_block", hc.HC_TRACK_PERSISTENT), ("whole_gpu", hc.HC_TRACK_GRID)):
+            st, dt = run([s], [g], predictor=hc.HC_PRED_QUADRATIC, mode=mode)
+            r[eng] = summary(st, dt)
+        out[f"table4_dim40_deg{deg}_qd"] = r
+    fam = [synth.paper_dim_degree(20 + j, 20, 20, 10) for j in range(3)]
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    r = {"n": 20, "monomials": systems[0].nmon, "degree": 10, "systems": 3}
+    for name, pred in (("secant", hc.HC_PRED_SECANT), ("quadratic", hc.HC_PRED_QUADRATIC)):
+        st, dt = run(systems, gammas, predictor=pred)
+        r[name] = summary(st, dt)
+    out["tables23_dim20_deg10_qd"] = r
+    return out
+
+
+def common_support_bench(torch, hc, synth, peak_gops=None, npts=8192):
+    """The system behind Table 1 (40 variables, one support of 200 monomials shared by all
+    40 polynomials, degree 40 on average and 80 at most), complex DD, at npts unit-torus
+    points: evaluation with Jacobian in the per-term and in the shared-monomial scheme
+    (points/s, and FP64 instructions per second from the library's per-point counts
+    against the measured peak), and the split of a Newton step (FP64 LU + DD refinement)
+    between evaluation and solve, the split Table 1 reports."""
+    import numpy as np
+    s, gamma = synth.common_support_system(1)
+    rng = np.random.default_rng(77)
+    pts = synth.torus_points(rng, npts, s.n)
+    sysh = hc.system_from(s, 2, gamma)
+    x0 = torch.from_numpy(hc.to_soa(pts, 2)).cuda()
+    x = x0.clone()
+    f = torch.empty((2, 2, s.npoly, npts), dtype=torch.float64, device="cuda")
+    J = torch.empty((2, 2, s.npoly, s.n, npts), dtype=torch.float64, device="cuda")
+    res = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    st = torch.zeros(npts, dtype=torch.int32, device="cuda")
+    sw = torch.zeros(npts, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    _, ops_term, ops_shared = sysh.eval_mode()
+
+    def timed(fn, reps=3):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        best = 1e30
+        for _ in range(reps):
+            x.copy_(x0)
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, ev0.elapsed_time(ev1))
+        return best
+
+    out = {"n": s.n, "monomials": s.nmon, "distinct_monomials": 200, "npts": npts,
+           "fp64_per_point_per_term": ops_term, "fp64_per_point_shared": ops_shared}
+    for name, mode, ops in (("per_term", hc.HC_EVAL_PER_TERM, ops_term), ("shared", hc.HC_EVAL_SHARED, ops_shared)):
+        sysh.set_eval_mode(mode)
+        ms_eval = timed(lambda: hc.hc_eval_jac(sysh, npts, 0.5, x, f, J, stream))
+        ms_newton = timed(lambda: hc.hc_newton_step(sysh, npts, 0.5, x, hc.HC_LU_FP64_REFINE, 4, res, st, sw, stream))
+        gops = ops * npts / (ms_eval * 1e-3) / 1e9
+        out[name] = {"eval_points_per_s": npts / (ms_eval * 1e-3), "eval_ms": ms_eval,
+                     "newton_step_ms": ms_newton, "eval_share_of_newton_step": ms_eval / ms_newton,
+                     "eval_fp64_gops": gops, "eval_fp64_frac_of_measured_peak": gops / peak_gops if peak_gops else None}
+    out["shared_speedup"] = out["per_term"]["eval_ms"] / out["shared"]["eval_ms"]
+    sysh.free()
     return out
 
 
@@ -410,7 +519,9 @@ def run_gpu(args):
         ms_qd = ev0.elapsed_time(ev1)
         sysq.free()
         del xq, fq, Jq
-        extras = {"tracker": tracker_bench(torch, hc, synth),
+        extras = {"tracker": tracker_bench(torch, hc, synth, peak_gops),
+                  "paper_tables": paper_tables_bench(torch, hc, synth),
+                  "common_support_table1": common_support_bench(torch, hc, synth, peak_gops),
                   "eval_jac_qd_points_per_s": q / (ms_qd * 1e-3),
                   "eval_jac_qd_fp64_gops": opcount.eval_ops_per_point(s, 4) * q / (ms_qd * 1e-3) / 1e9,
                   "newton_native_dd_lu_points_per_s": npts / (ms_native * 1e-3),

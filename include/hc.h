@@ -208,6 +208,25 @@ typedef struct {
     int32_t accepted;    /* 1 if the stage was accepted */
 } hc_step_record;
 
+/* Evaluation schemes of the point kernels (hc_eval_jac, hc_newton_step). */
+#define HC_EVAL_AUTO 0      /* the scheme with fewer FP64 instructions, by at least 10 % */
+#define HC_EVAL_PER_TERM 1  /* each term's monomial and partials with its coefficient folded
+                               into the common factor (Sec. 6) */
+#define HC_EVAL_SHARED 2    /* each distinct monomial and its partials once per point, then
+                               one coefficient product per term and partial: for systems
+                               whose polynomials share monomials (a common support, the
+                               40 x 40 system of Sec. 4 behind Table 1) */
+
+/* Choose the evaluation scheme of sys (HC_EVAL_AUTO restores the choice made at load).
+ * Both schemes compute the same values up to rounding.  No device work.  Errors:
+ * HC_EINVAL for a NULL sys or an unknown mode. */
+int hc_system_set_eval_mode(hc_system *sys, int mode);
+
+/* The scheme in use (HC_EVAL_PER_TERM or HC_EVAL_SHARED), and the FP64 instructions per
+ * point of each scheme's evaluation with Jacobian, counted at load with complex
+ * double-double weights (either pointer may be NULL).  HC_EINVAL for a NULL sys. */
+int hc_system_eval_mode(const hc_system *sys, double *ops_per_term, double *ops_shared);
+
 /* Fill *opts with the defaults listed above. */
 void hc_track_opts_default(hc_track_opts *opts);
 

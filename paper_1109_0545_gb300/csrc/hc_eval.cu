@@ -22,10 +22,19 @@ __global__ void __launch_bounds__(256) k_powers(int n, int npts, int max_exp,
     }
 }
 
+template <int L>
+void launch_powers(int grid, int n, int npts, int max_exp, const double *X, double *PW, cudaStream_t st)
+{
+    k_powers<L><<<grid, 256, 0, st>>>(n, npts, max_exp, X, PW);
+}
+template void launch_powers<1>(int, int, int, int, const double *, double *, cudaStream_t);
+template void launch_powers<2>(int, int, int, int, const double *, double *, cudaStream_t);
+template void launch_powers<4>(int, int, int, int, const double *, double *, cudaStream_t);
+
 // Persistent warps over tasks (32-point tile, group of rows); the row groups of one tile
 // are consecutive tasks, so the warps of a block share their points' data in L1.
 template <int L, bool JAC>
-__global__ void __launch_bounds__(128) k_eval_pts(DevSys S, int npts, double t,
+__global__ void __launch_bounds__(128, L == 4 ? 3 : 1) k_eval_pts(DevSys S, int npts, double t,
                                                   const double *__restrict__ X,
                                                   const double *__restrict__ PW,
                                                   double *__restrict__ F, double *__restrict__ J,
@@ -130,6 +139,13 @@ int hc_check_eval_args(const hc_system *s, int npts, double t)
 int hc_eval_dispatch(hc_system *s, int npts, double t, const double *x, double *pw, double *f,
                      double *J, const EvalTiles &tiles, cudaStream_t st)
 {
+    if (s->eval_shared) {
+        switch (s->prec) {
+        case 1: return launch_eval_shared<1>(s->dev, npts, t, x, pw, f, J, st);
+        case 2: return launch_eval_shared<2>(s->dev, npts, t, x, pw, f, J, st);
+        case 4: return launch_eval_shared<4>(s->dev, npts, t, x, pw, f, J, st);
+        }
+    }
     switch (s->prec) {
     case 1: return launch_eval<1>(s->dev, npts, t, x, pw, f, J, tiles, st);
     case 2: return launch_eval<2>(s->dev, npts, t, x, pw, f, J, tiles, st);

@@ -11,6 +11,13 @@ namespace hc {
 template <int L>
 int launch_eval(const DevSys &S, int npts, double t, const double *X, double *PW, double *F,
                 double *J, const EvalTiles &tiles, cudaStream_t st);
+// the shared-monomial scheme (hc_shared.cu)
+template <int L>
+int launch_eval_shared(const DevSys &S, int npts, double t, const double *X, double *PW, double *F, double *J,
+                       cudaStream_t st);
+// the power table PW of the points X (k_powers)
+template <int L>
+void launch_powers(int grid, int n, int npts, int max_exp, const double *X, double *PW, cudaStream_t st);
 }
 
 EvalTiles &hc_eval_tiles();  // process-wide tile choice (hc_set_tiles)

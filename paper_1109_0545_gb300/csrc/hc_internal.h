@@ -28,6 +28,16 @@ struct DevSys {
                               // its value; original monomial order within an entry
     const int32_t *eperm;     // [npoly*(n+1)] entries by contribution count, descending (ties
                               // by entry), so the lanes of a warp sum lists of equal length
+    // shared-monomial evaluation (polynomials that repeat one another's monomials, e.g. a
+    // common support): the distinct non-constant monomials and the terms that use each
+    int nuniq;                // distinct non-constant monomials (0: tables not built)
+    const int32_t *uvar_ptr;  // [nuniq+1] into uvar_pack
+    const int32_t *uvar_pack; // index | exponent << 16, as var_pack
+    const int32_t *uuse_ptr;  // [nuniq+1] into uuse
+    const int32_t *uuse;      // term index m of each use, increasing within a monomial
+    const int32_t *term_row;  // [nmon] the polynomial of term m
+    const int32_t *cptr;      // [npoly+1] into cterm
+    const int32_t *cterm;     // constant terms (k = 0) of each polynomial, increasing
 };
 
 struct hc_system {
@@ -42,6 +52,13 @@ struct hc_system {
     size_t ws_bytes;
     // host copies (used to build per-kernel layouts)
     int32_t *h_mon_ptr, *h_var_ptr, *h_var_pack, *h_deg;
+    // evaluation scheme of the point kernels: 0 per term (each term's monomial evaluated
+    // with its coefficient folded in), 1 shared (each distinct monomial once, then the
+    // coefficient products); chosen at load by the FP64 instruction counts of the two,
+    // changeable with hc_system_set_eval_mode
+    int eval_shared;
+    double ops_term, ops_shared;  // FP64 instructions per point of each scheme (DD weights)
+    void *dev_shared;             // device block of the shared tables
 };
 
 // error reporting (thread-local message)

@@ -1,0 +1,150 @@
+// hc_shared.cu -- evaluation with shared monomials, one lane per point: for systems whose
+// polynomials repeat one another's monomials (a common support, as in the experiment of
+// Sec. 4 that reports the cost split of Table 1), each distinct monomial and its partial
+// derivatives are evaluated once per point (the scheme of Sec. 6 with coefficient 1), then
+// every term that uses it adds its coefficient times these values to its polynomial and
+// Jacobian row (Coefficient_Product of Alg. 4.1, done per term).
+#include "hc_eval.cuh"
+
+namespace hc {
+
+template <int L, bool JAC>
+__device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool live, double t, const C<L> &gs,
+                                  double *__restrict__ F, double *__restrict__ J)
+{
+    const int n = S.n, npts = V.npts, p = V.p;
+    const size_t fplane = (size_t)S.npoly * npts;
+    const size_t jplane = (size_t)S.npoly * n * npts;
+    // constant terms, zero Jacobian rows
+    if (live)
+        for (int i = 0; i < S.npoly; i++) {
+            C<L> fi = c_zero<L>();
+            for (int q = __ldg(S.cptr + i); q < __ldg(S.cptr + i + 1); q++)
+                fi = c_add(fi, ld_c<L>(S.coef + (size_t)__ldg(S.cterm + q) * 2 * L, 1, 0));
+            st_c<L>(F, fplane, (size_t)i * npts + p, fi);
+            if (JAC)
+                for (int j = 0; j < n; j++) st_c<L>(J, jplane, ((size_t)i * n + j) * npts + p, c_zero<L>());
+        }
+    C<L> d[HC_KLOCAL];
+    for (int u = 0; u < S.nuniq; u++) {
+        const int q0 = __ldg(S.uvar_ptr + u), k = __ldg(S.uvar_ptr + u + 1) - q0;
+        // common factor prod x_j^(a_j - 1) over a_j >= 2; `one` while it is exactly 1
+        C<L> cf = c_from<L>(1.0, 0.0);
+        bool one = true;
+        for (int j = 0; j < k; j++) {
+            const int pk = __ldg(S.uvar_pack + q0 + j), e = pk >> 16;
+            if (e >= 2) {
+                cf = one ? V.pw(pk & 0xffff, e - 1) : c_mul_nn(cf, V.pw(pk & 0xffff, e - 1));
+                one = false;
+            }
+        }
+        // prefix products d_j = cf x_{i1} ... x_{i(j-1)}, the value, the backward sweep
+        d[0] = cf;
+        for (int j = 1; j < k; j++) {
+            const C<L> xj = V.x(__ldg(S.uvar_pack + q0 + j - 1) & 0xffff);
+            d[j] = (j == 1 && one) ? xj : c_mul_nn(d[j - 1], xj);
+        }
+        const int pkl = __ldg(S.uvar_pack + q0 + k - 1);
+        const C<L> xl = V.x(pkl & 0xffff);
+        const C<L> value = (k == 1 && one) ? xl : c_mul_nn(d[k - 1], xl);
+        if (JAC) {
+            d[k - 1] = c_scale_int(d[k - 1], pkl >> 16);
+            C<L> suf = xl;
+            for (int j = k - 2; j >= 0; j--) {
+                const int pk = __ldg(S.uvar_pack + q0 + j);
+                d[j] = c_scale_int((j == 0 && one) ? suf : c_mul_nn(d[j], suf), pk >> 16);
+                if (j > 0) suf = c_mul_nn(suf, V.x(pk & 0xffff));
+            }
+        }
+        // every term using the monomial: f_i += c value, J_{i,ij} += c a_j x^(a - e_j)
+        for (int r = __ldg(S.uuse_ptr + u); r < __ldg(S.uuse_ptr + u + 1); r++) {
+            const int m = __ldg(S.uuse + r), i = __ldg(S.term_row + m);
+            const C<L> c = ld_c<L>(S.coef + (size_t)m * 2 * L, 1, 0);
+            if (!live) continue;
+            const size_t fo = (size_t)i * npts + p;
+            st_c<L>(F, fplane, fo, c_add(ld_c<L>(F, fplane, fo), c_mul_nn(c, value)));
+            if (JAC)
+                for (int j = 0; j < k; j++) {
+                    const size_t o = ((size_t)i * n + (__ldg(S.uvar_pack + q0 + j) & 0xffff)) * npts + p;
+                    st_c<L>(J, jplane, o, c_add(ld_c<L>(J, jplane, o), c_mul_nn(c, d[j])));
+                }
+        }
+    }
+    if (t >= 0.0 && live) {
+        // homotopy assembly, as in eval_rows_point
+        for (int i = 0; i < S.npoly; i++) {
+            const int dg = __ldg(S.deg + i);
+            const C<L> xi = V.x(i);
+            const C<L> xd1 = c_pow(xi, dg - 1);
+            C<L> g = c_mul(xd1, xi);
+            g.re = r_sub(g.re, r_from<L>(1.0));
+            const size_t fo = (size_t)i * npts + p;
+            st_c<L>(F, fplane, fo, c_add(c_mul(gs, g), c_mul_d(ld_c<L>(F, fplane, fo), t)));
+            if (JAC)
+                for (int j = 0; j < n; j++) {
+                    const size_t o = ((size_t)i * n + j) * npts + p;
+                    C<L> v = c_mul_d(ld_c<L>(J, jplane, o), t);
+                    if (j == i) v = c_add(v, c_mul(gs, c_scale_int(xd1, dg)));
+                    st_c<L>(J, jplane, o, v);
+                }
+        }
+    }
+}
+
+// persistent warps over 32-point tiles
+template <int L, bool JAC>
+__global__ void __launch_bounds__(128) k_eval_shared(DevSys S, int npts, double t, const double *__restrict__ X,
+                                                     const double *__restrict__ PW, double *__restrict__ F,
+                                                     double *__restrict__ J)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int ntiles = (npts + 31) >> 5;
+    const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
+    for (int tile = warp; tile < ntiles; tile += nwarps) {
+        const int p = tile * 32 + lane;
+        const bool live = p < npts;
+        PointView<L> V{X, PW, (size_t)S.n * npts, npts, live ? p : npts - 1};
+        eval_shared_point<L, JAC>(S, V, live, t, gs, F, J);
+    }
+}
+
+template <int L>
+int launch_eval_shared(const DevSys &S, int npts, double t, const double *X, double *PW, double *F, double *J,
+                       cudaStream_t st)
+{
+    const int sms = hc_num_sms();
+    if (S.max_exp > 2) {
+        const size_t work = (size_t)S.n * npts;
+        size_t g = (work + 255) / 256;
+        if (g > (size_t)sms * 8) g = (size_t)sms * 8;
+        launch_powers<L>((int)g, S.n, npts, S.max_exp, X, PW, st);
+    }
+    const int ntiles = (npts + 31) / 32;
+    int occ = 1;
+    if (J)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, true>, 128, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, false>, 128, 0);
+    if (occ < 1) occ = 1;
+    long long grid = (long long)sms * occ;
+    const long long need = (ntiles + 3) / 4;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    hc_prof_mark(st, true);
+    if (J)
+        k_eval_shared<L, true><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J);
+    else
+        k_eval_shared<L, false><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J);
+    hc_prof_mark(st, false);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hc_cuda_fail(e, "k_eval_shared launch");
+    return HC_SUCCESS;
+}
+
+template int launch_eval_shared<1>(const DevSys &, int, double, const double *, double *, double *, double *, cudaStream_t);
+template int launch_eval_shared<2>(const DevSys &, int, double, const double *, double *, double *, double *, cudaStream_t);
+template int launch_eval_shared<4>(const DevSys &, int, double, const double *, double *, double *, double *, cudaStream_t);
+
+}  // namespace hc

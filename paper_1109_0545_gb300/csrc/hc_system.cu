@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 
 #include "hc_internal.h"
 
@@ -144,6 +145,8 @@ static int validate(int n, int npoly, const int32_t *mon_ptr, const int32_t *var
     if (!std::isfinite(gamma[0]) || !std::isfinite(gamma[1])) return hc_fail(HC_EINVAL, "gamma not finite");
     return HC_SUCCESS;
 }
+
+static int build_shared_tables(hc_system *s);
 
 extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *mon_ptr,
                               const int32_t *var_ptr, const int32_t *var_idx,
@@ -304,15 +307,142 @@ extern "C" int hc_system_load(hc_system **out, int n, int npoly, const int32_t *
     d.coef = (const double *)(b + o_coef);
     d.gre = gamma[0];
     d.gim = gamma[1];
+    const int rc_shared = build_shared_tables(s);
+    if (rc_shared) {
+        hc_system_free(s);
+        return rc_shared;
+    }
     *out = s;
     return HC_SUCCESS;
+}
+
+// FP64 instructions (complex DD weights) of one monomial's evaluation with its partials:
+// the common factor, prefix products, value and backward sweep (with_coef: the
+// coefficient folded into the common factor), and the integer scalings of the partials
+static double monomial_ops(const int32_t *pack, int k, bool with_coef)
+{
+    if (k == 0) return 0.0;
+    int n2 = 0;
+    double scale = 0.0;
+    for (int q = 0; q < k; q++) {
+        const int e = pack[q] >> 16;
+        n2 += e >= 2;
+        if (e != 1 && (e & (e - 1)) != 0) scale += 12.0;
+    }
+    int mults = n2 + (k >= 2 ? 3 * k - 3 : 1);
+    if (!with_coef && n2 == 0) mults -= 1;  // the common factor is exactly 1
+    return 26.0 * mults + scale;
+}
+
+// The shared-monomial tables: distinct non-constant monomials in order of first use, the
+// terms using each, the polynomial of each term, each polynomial's constant terms; and the
+// FP64 counts of the per-term and shared evaluation schemes.
+static int build_shared_tables(hc_system *s)
+{
+    const int nmon = s->nmon, npoly = s->npoly;
+    const int32_t *vp = s->h_var_ptr, *pack = s->h_var_pack;
+    std::map<std::vector<int32_t>, int> ids;
+    std::vector<int32_t> uid((size_t)nmon, -1), first, term_row((size_t)nmon), cptr((size_t)npoly + 1, 0), cterm;
+    double ops_term = 0.0, ops_shared = 0.0;
+    for (int i = 0; i < npoly; i++) {
+        for (int m = s->h_mon_ptr[i]; m < s->h_mon_ptr[i + 1]; m++) {
+            term_row[m] = i;
+            const int k = vp[m + 1] - vp[m];
+            if (k == 0) {
+                cterm.push_back(m);
+                ops_term += 16.0;
+                ops_shared += 16.0;
+                continue;
+            }
+            std::vector<int32_t> key(pack + vp[m], pack + vp[m + 1]);
+            auto it = ids.find(key);
+            if (it == ids.end()) {
+                it = ids.emplace(std::move(key), (int)first.size()).first;
+                first.push_back(m);
+                ops_shared += monomial_ops(pack + vp[m], k, false);
+            }
+            uid[m] = it->second;
+            ops_term += monomial_ops(pack + vp[m], k, true) + 16.0 * (k + 1);
+            ops_shared += 42.0 * (k + 1);
+        }
+        cptr[i + 1] = (int32_t)cterm.size();
+    }
+    const int nuniq = (int)first.size();
+    std::vector<int32_t> uvar_ptr((size_t)nuniq + 1, 0), uvar_pack, uuse_ptr((size_t)nuniq + 1, 0), uuse;
+    for (int u = 0; u < nuniq; u++) {
+        const int m = first[u];
+        uvar_pack.insert(uvar_pack.end(), pack + vp[m], pack + vp[m + 1]);
+        uvar_ptr[u + 1] = (int32_t)uvar_pack.size();
+    }
+    for (int m = 0; m < nmon; m++)
+        if (uid[m] >= 0) uuse_ptr[uid[m] + 1]++;
+    for (int u = 0; u < nuniq; u++) uuse_ptr[u + 1] += uuse_ptr[u];
+    uuse.resize((size_t)uuse_ptr[nuniq]);
+    {
+        std::vector<int32_t> fill(uuse_ptr.begin(), uuse_ptr.end() - 1);
+        for (int m = 0; m < nmon; m++)
+            if (uid[m] >= 0) uuse[fill[uid[m]]++] = m;
+    }
+    // one device block: uvar_ptr | uvar_pack | uuse_ptr | uuse | term_row | cptr | cterm
+    auto sz = [](size_t n) { return hc_align256(sizeof(int32_t) * (n > 0 ? n : 1)); };
+    const size_t o1 = 0, o2 = o1 + sz(uvar_ptr.size()), o3 = o2 + sz(uvar_pack.size()),
+                 o4 = o3 + sz(uuse_ptr.size()), o5 = o4 + sz(uuse.size()), o6 = o5 + sz(term_row.size()),
+                 o7 = o6 + sz(cptr.size()), total = o7 + sz(cterm.size());
+    cudaError_t e = cudaMalloc(&s->dev_shared, total);
+    if (e != cudaSuccess) return hc_cuda_fail(e, "cudaMalloc(shared tables)");
+    char *b = (char *)s->dev_shared;
+    auto put = [&](size_t off, const std::vector<int32_t> &v) {
+        if (e == cudaSuccess && !v.empty())
+            e = cudaMemcpy(b + off, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
+    };
+    put(o1, uvar_ptr);
+    put(o2, uvar_pack);
+    put(o3, uuse_ptr);
+    put(o4, uuse);
+    put(o5, term_row);
+    put(o6, cptr);
+    put(o7, cterm);
+    if (e != cudaSuccess) return hc_cuda_fail(e, "cudaMemcpy(shared tables)");
+    DevSys &d = s->dev;
+    d.nuniq = nuniq;
+    d.uvar_ptr = (const int32_t *)(b + o1);
+    d.uvar_pack = (const int32_t *)(b + o2);
+    d.uuse_ptr = (const int32_t *)(b + o3);
+    d.uuse = (const int32_t *)(b + o4);
+    d.term_row = (const int32_t *)(b + o5);
+    d.cptr = (const int32_t *)(b + o6);
+    d.cterm = (const int32_t *)(b + o7);
+    s->ops_term = ops_term;
+    s->ops_shared = ops_shared;
+    // the shared scheme when it saves at least a tenth of the FP64 instructions
+    s->eval_shared = ops_shared < 0.9 * ops_term;
+    return HC_SUCCESS;
+}
+
+extern "C" int hc_system_set_eval_mode(hc_system *s, int mode)
+{
+    if (!s) return hc_fail(HC_EINVAL, "sys is NULL");
+    if (mode == HC_EVAL_AUTO) s->eval_shared = s->ops_shared < 0.9 * s->ops_term;
+    else if (mode == HC_EVAL_PER_TERM) s->eval_shared = 0;
+    else if (mode == HC_EVAL_SHARED) s->eval_shared = 1;
+    else return hc_fail(HC_EINVAL, "unknown evaluation mode %d", mode);
+    return HC_SUCCESS;
+}
+
+extern "C" int hc_system_eval_mode(const hc_system *s, double *ops_per_term, double *ops_shared)
+{
+    if (!s) return hc_fail(HC_EINVAL, "sys is NULL");
+    if (ops_per_term) *ops_per_term = s->ops_term;
+    if (ops_shared) *ops_shared = s->ops_shared;
+    return s->eval_shared ? HC_EVAL_SHARED : HC_EVAL_PER_TERM;
 }
 
 extern "C" void hc_system_free(hc_system *s)
 {
     if (!s) return;
-    if (s->dev_block || s->ws) cudaDeviceSynchronize();
+    if (s->dev_block || s->ws || s->dev_shared) cudaDeviceSynchronize();
     if (s->dev_block) cudaFree(s->dev_block);
+    if (s->dev_shared) cudaFree(s->dev_shared);
     if (s->ws) cudaFree(s->ws);
     free(s->h_mon_ptr);
     free(s->h_var_ptr);

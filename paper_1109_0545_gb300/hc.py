@@ -53,6 +53,7 @@ STEP_RECORD_DTYPE = np.dtype([("t", "f8"), ("lam", "f8"), ("res_first", "f8"), (
                               ("pc_dist", "f8"), ("cond_log10", "f8"), ("iters", "i4"),
                               ("accepted", "i4")])
 HC_PRED_SECANT, HC_PRED_QUADRATIC = 0, 1
+HC_EVAL_AUTO, HC_EVAL_PER_TERM, HC_EVAL_SHARED = 0, 1, 2
 HC_TRACK_PERSISTENT, HC_TRACK_GRAPH, HC_TRACK_GRID = 0, 1, 2
 
 
@@ -109,6 +110,10 @@ def load(build_if_missing: bool = True):
         L.hc_mlp_adamw.restype = i
         L.hc_mlp_forward.argtypes = [vp, i, vp, vp, vp]
         L.hc_mlp_forward.restype = i
+        L.hc_system_set_eval_mode.argtypes = [vp, i]
+        L.hc_system_set_eval_mode.restype = i
+        L.hc_system_eval_mode.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+        L.hc_system_eval_mode.restype = i
         L.hc_eval_jac_noalloc.argtypes = [vp, i, d, vp, vp, vp, vp]
         L.hc_eval_jac_noalloc.restype = i
         L.hc_prof_enable.argtypes = [i]
@@ -163,6 +168,18 @@ class System:
         _check("hc_system_info", load().hc_system_info(self.handle, *[ct.byref(v) for v in vals]))
         keys = ("n", "npoly", "nmon", "nvar", "prec", "max_exp", "max_deg")
         return {k: v.value for k, v in zip(keys, vals)}
+
+    def set_eval_mode(self, mode: int) -> None:
+        """hc_system_set_eval_mode: HC_EVAL_AUTO, HC_EVAL_PER_TERM or HC_EVAL_SHARED."""
+        _check("hc_system_set_eval_mode", load().hc_system_set_eval_mode(self.handle, int(mode)))
+
+    def eval_mode(self) -> tuple[int, float, float]:
+        """hc_system_eval_mode: (scheme in use, FP64 per point per term, FP64 per point shared)."""
+        a, b = ct.c_double(), ct.c_double()
+        r = load().hc_system_eval_mode(self.handle, ct.byref(a), ct.byref(b))
+        if r < 0:
+            _check("hc_system_eval_mode", r)
+        return r, a.value, b.value
 
     def free(self):
         if self.handle:

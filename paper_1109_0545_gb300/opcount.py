@@ -69,3 +69,23 @@ def powers_ops_per_point(s, L: int) -> int:
     """FP64 instructions of the power-table kernel for one point."""
     emax = int(s.var_exp.max()) if len(s.var_exp) else 1
     return s.n * max(emax - 2, 0) * C_MUL[L]
+
+
+def lu64_ops(n: int) -> int:
+    """FP64 instructions of the block FP64 LU (`block_lu64`) of an n x n complex matrix:
+    per column k the pivot moduli (3 per row), the multipliers (4 each) and the trailing
+    update (4 per entry, a complex FMA)."""
+    return sum(3 * (n - k) + 4 * (n - k - 1) + 4 * (n - k - 1) ** 2 for k in range(n))
+
+
+def lu64_solve_ops(n: int) -> int:
+    """FP64 instructions of one solve with the FP64 factors: forward and back substitution,
+    4 per complex multiply-add, 4 per diagonal product."""
+    return 4 * (n * (n - 1) // 2) * 2 + 4 * n
+
+
+def newton_iteration_ops(s, L: int) -> int:
+    """FP64 instructions of one Newton iteration of the path tracker's FP64-LU mode, refinement
+    sweeps not counted (so a lower bound): evaluation of h and its Jacobian, the FP64 LU and
+    the first solve."""
+    return eval_ops_per_point(s, L) + lu64_ops(s.n) + lu64_solve_ops(s.n)

@@ -113,15 +113,47 @@ def unit_complex(rng: np.random.Generator) -> complex:
     return complex(np.cos(th), np.sin(th))
 
 
-def regular_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
-                   lead: int) -> System:
-    """A random system (as random_system) plus, in polynomial i, the monomial x_i^D with
-    coefficient 1, D = max(lead, 1 + the largest total degree of the other monomials).
-    Its leading forms then vanish together only at 0, so no path of the total-degree
-    homotopy goes to infinity: test systems whose paths should end at roots.  Each
-    polynomial also gets a constant term, so that x = 0 (a singular root of a system
-    without constants) is not a root."""
-    s = random_system(rng, n, mons_per_poly, k, exps, const_term=True)
+def fixed_degree_system(rng: np.random.Generator, n: int, mons_per_poly, degree: int, kmax: int = 8,
+                        const_term: bool = False) -> System:
+    """A random system whose monomials all have total degree `degree` (the shapes of the
+    paper's experiments, "monomials of degree D", Sec. 5 and 7): per monomial k uniform in
+    {1..min(degree, kmax, n)}, a uniform random k-subset of the variables, and exponents a
+    uniform random composition of `degree` into k positive parts (k-1 distinct cut points
+    drawn from {1..degree-1}); theta uniform.  Draw order per monomial: k, support, cut
+    points, theta; then a constant-term theta if requested."""
+    mon_ptr = [0]
+    var_ptr = [0]
+    idx: list[np.ndarray] = []
+    ex: list[np.ndarray] = []
+    thetas: list[float] = []
+    kk_max = max(1, min(degree, kmax, n))
+    for _ in range(n):
+        m_i = _draw(rng, mons_per_poly)
+        for _ in range(m_i):
+            kk = int(rng.integers(1, kk_max + 1))
+            sup = np.sort(rng.choice(n, size=kk, replace=False)).astype(np.int32)
+            cuts = np.sort(rng.choice(np.arange(1, degree), size=kk - 1, replace=False)) if kk > 1 else np.zeros(0)
+            e = np.diff(np.concatenate([[0], cuts, [degree]])).astype(np.int32)
+            idx.append(sup)
+            ex.append(e)
+            var_ptr.append(var_ptr[-1] + kk)
+            thetas.append(rng.uniform(0.0, 2.0 * np.pi))
+        cnt = m_i
+        if const_term:
+            var_ptr.append(var_ptr[-1])
+            thetas.append(rng.uniform(0.0, 2.0 * np.pi))
+            cnt += 1
+        mon_ptr.append(mon_ptr[-1] + cnt)
+    th = np.array(thetas)
+    return System(n=n, npoly=n, mon_ptr=np.array(mon_ptr, dtype=np.int32),
+                  var_ptr=np.array(var_ptr, dtype=np.int32),
+                  var_idx=np.concatenate(idx).astype(np.int32), var_exp=np.concatenate(ex).astype(np.int32),
+                  coef=np.cos(th) + 1j * np.sin(th))
+
+
+def _with_leading_powers(s: System, lead: int) -> System:
+    """s plus, in polynomial i, the monomial x_i^D with coefficient 1, D = max(lead, 1 + the
+    largest total degree in s), placed last in the polynomial."""
     top = 0
     for m in range(s.nmon):
         top = max(top, int(s.var_exp[s.var_ptr[m]:s.var_ptr[m + 1]].sum()))
@@ -129,7 +161,7 @@ def regular_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
     mon_ptr = [0]
     var_ptr = [0]
     idx, ex, coef = [], [], []
-    for i in range(n):
+    for i in range(s.npoly):
         for m in range(s.mon_ptr[i], s.mon_ptr[i + 1]):
             q0, q1 = s.var_ptr[m], s.var_ptr[m + 1]
             idx.extend(s.var_idx[q0:q1])
@@ -141,9 +173,20 @@ def regular_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
         var_ptr.append(var_ptr[-1] + 1)
         coef.append(1.0 + 0j)
         mon_ptr.append(len(coef))
-    return System(n=n, npoly=n, mon_ptr=np.array(mon_ptr, np.int32),
+    return System(n=s.n, npoly=s.npoly, mon_ptr=np.array(mon_ptr, np.int32),
                   var_ptr=np.array(var_ptr, np.int32), var_idx=np.array(idx, np.int32),
                   var_exp=np.array(ex, np.int32), coef=np.array(coef))
+
+
+def regular_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
+                   lead: int) -> System:
+    """A random system (as random_system) plus, in polynomial i, the monomial x_i^D with
+    coefficient 1, D = max(lead, 1 + the largest total degree of the other monomials).
+    Its leading forms then vanish together only at 0, so no path of the total-degree
+    homotopy goes to infinity: test systems whose paths should end at roots.  Each
+    polynomial also gets a constant term, so that x = 0 (a singular root of a system
+    without constants) is not a root."""
+    return _with_leading_powers(random_system(rng, n, mons_per_poly, k, exps, const_term=True), lead)
 
 
 # ---------------------------------------------------------------------------------------
@@ -184,4 +227,39 @@ def large_path_qd(seed: int = 4, n: int = 96, mons: int = 1024, k: int = 12, exp
     {1..5}.  Returns (system, gamma)."""
     rng = np.random.default_rng(seed)
     s = random_system(rng, n, mons, k, exps)
+    return s, unit_complex(rng)
+
+
+def paper_dim_degree(seed: int, n: int, mons: int, degree: int, regular: bool = True):
+    """One system of the shapes of the paper's one-path experiments (Tables 2-5): n x n,
+    `mons` monomials of total degree `degree` per polynomial.  regular: plus a constant
+    and x_i^(degree+1) in polynomial i (the leading powers make every path of the
+    total-degree homotopy end at a regular root).  Returns (system, gamma)."""
+    rng = np.random.default_rng([seed, n, mons, degree])
+    s = fixed_degree_system(rng, n, mons, degree, const_term=regular)
+    if regular:
+        s = _with_leading_powers(s, degree + 1)
+    return s, unit_complex(rng)
+
+
+def common_support_system(seed: int, n: int = 40, nuniq: int = 200, dmax: int = 80, kmax: int = 32):
+    """A system whose n polynomials share one support of `nuniq` monomials (the system
+    behind the cost split of Table 1, Sec. 4: 40 variables, 200 monomials of degree 40 on
+    average and 80 at most): per monomial a degree d uniform in {1..dmax}, k uniform in
+    {1..min(d, n, kmax)}, a uniform random k-subset, exponents a uniform random
+    composition of d into k parts; then a coefficient theta per (polynomial, monomial),
+    polynomial by polynomial.  Returns (system, gamma)."""
+    rng = np.random.default_rng([seed, n, nuniq, dmax])
+    sup, exps = [], []
+    for _ in range(nuniq):
+        d = int(rng.integers(1, dmax + 1))
+        kk = int(rng.integers(1, min(d, n, kmax) + 1))
+        sup.append(np.sort(rng.choice(n, size=kk, replace=False)).astype(np.int32))
+        cuts = np.sort(rng.choice(np.arange(1, d), size=kk - 1, replace=False)) if kk > 1 else np.zeros(0)
+        exps.append(np.diff(np.concatenate([[0], cuts, [d]])).astype(np.int32))
+    th = rng.uniform(0.0, 2.0 * np.pi, size=(n, nuniq))
+    var_ptr = np.concatenate([[0], np.cumsum([len(x) for x in sup] * n)]).astype(np.int32)
+    s = System(n=n, npoly=n, mon_ptr=(np.arange(n + 1) * nuniq).astype(np.int32), var_ptr=var_ptr,
+               var_idx=np.concatenate(sup * n).astype(np.int32), var_exp=np.concatenate(exps * n).astype(np.int32),
+               coef=(np.cos(th) + 1j * np.sin(th)).ravel())
     return s, unit_complex(rng)

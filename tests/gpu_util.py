@@ -20,9 +20,12 @@ def dev(torch, a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def gpu_eval(torch, s, gamma, L, pts_limbs, t, jac=True):
-    """Evaluate on the GPU; returns (f, J) as limbs [npts][rows][(n)][2][L]."""
+def gpu_eval(torch, s, gamma, L, pts_limbs, t, jac=True, mode=None):
+    """Evaluate on the GPU (evaluation scheme `mode`, default the library's choice);
+    returns (f, J) as limbs [npts][rows][(n)][2][L]."""
     sysh = hc.system_from(s, L, gamma)
+    if mode is not None:
+        sysh.set_eval_mode(mode)
     npts = pts_limbs.shape[0]
     x = dev(torch, hc.to_soa(None, L, pts_limbs))
     f = torch.zeros((2, L, s.npoly, npts), dtype=torch.float64, device="cuda")
@@ -43,8 +46,10 @@ def oracle_eval(s, gamma, L, pts_limbs, t, jac=True, threads=True):
     return f, J
 
 
-def gpu_newton(torch, s, gamma, L, pts_limbs, t, lu_mode, max_refine=4):
+def gpu_newton(torch, s, gamma, L, pts_limbs, t, lu_mode, max_refine=4, mode=None):
     sysh = hc.system_from(s, L, gamma)
+    if mode is not None:
+        sysh.set_eval_mode(mode)
     npts = pts_limbs.shape[0]
     x = dev(torch, hc.to_soa(None, L, pts_limbs))
     res = torch.zeros(npts, dtype=torch.float64, device="cuda")

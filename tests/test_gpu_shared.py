@@ -1,0 +1,79 @@
+"""The shared-monomial evaluation scheme (HC_EVAL_SHARED) against the oracle: a system
+with a common support (all polynomials on one set of monomials, the shape behind Table 1)
+and general sparse systems, values and Jacobians of f and of the homotopy, in complex
+double / DD / QD, several 32-point tiles with a ragged tail; the Newton step on it; and the
+load-time choice of the scheme."""
+import numpy as np
+import pytest
+
+from helpers import TOL, digits, rel_err_per_point
+from gpu_util import gpu_eval, gpu_newton, limbs_of, oracle_eval, torch_cuda
+import oracle
+from paper_1109_0545_gb300 import hc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("t", [-1.0, 0.6])
+def test_common_support_matches_oracle_in_both_schemes(L, t):
+    torch = torch_cuda()
+    s, gamma = synth.common_support_system(11, n=8, nuniq=20, dmax=12)
+    rng = np.random.default_rng(500 + L)
+    pts = limbs_of(synth.torus_points(rng, 70, 8), L)
+    fo, Jo = oracle_eval(s, gamma, L, pts, t)
+    for mode in (hc.HC_EVAL_SHARED, hc.HC_EVAL_PER_TERM):
+        f, J = gpu_eval(torch, s, gamma, L, pts, t, mode=mode)
+        ef, eJ = rel_err_per_point(f, fo), rel_err_per_point(J, Jo)
+        print(f"L={L} t={t} mode={mode}: f {digits(ef):.1f} digits, J {digits(eJ):.1f} digits")
+        assert np.all(ef <= TOL[L]) and np.all(eJ <= TOL[L])
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_shared_scheme_on_a_general_system_with_constants(L):
+    """Every structure the per-term kernel handles: constants, k = 1, repeated monomials
+    within a polynomial, values only."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(510)
+    s = synth.random_system(rng, 7, (3, 9), (1, 4), (1, 4), const_term=True)
+    gamma = synth.unit_complex(rng)
+    pts = limbs_of(synth.torus_points(rng, 45, 7), L)
+    for jac in (True, False):
+        fo, Jo = oracle_eval(s, gamma, L, pts, 0.3, jac=jac)
+        f, J = gpu_eval(torch, s, gamma, L, pts, 0.3, jac=jac, mode=hc.HC_EVAL_SHARED)
+        assert np.all(rel_err_per_point(f, fo) <= TOL[L])
+        if jac:
+            assert np.all(rel_err_per_point(J, Jo) <= TOL[L])
+
+
+def test_newton_step_with_shared_scheme_matches_oracle():
+    torch = torch_cuda()
+    s, gamma = synth.common_support_system(12, n=10, nuniq=30, dmax=10)
+    rng = np.random.default_rng(520)
+    pts = limbs_of(synth.torus_points(rng, 40, 10), 2)
+    x, res, st, sw = gpu_newton(torch, s, gamma, 2, pts, 0.5, hc.HC_LU_FP64_REFINE, max_refine=6,
+                                mode=hc.HC_EVAL_SHARED)
+    xo, reso, sto, swo = oracle.newton_step(s.as_dict(), s.coef_limbs(2), pts, 0.5,
+                                            np.array([gamma.real, gamma.imag]), hc.HC_LU_FP64_REFINE, 6)
+    assert np.array_equal(st, sto)
+    assert np.allclose(res, reso, rtol=1e-12, atol=0)
+    assert np.all(rel_err_per_point(x, xo) <= TOL[2])
+
+
+def test_scheme_choice_at_load():
+    torch_cuda()
+    s, g = synth.common_support_system(1)            # 40 x 200 shared monomials
+    h = hc.system_from(s, 2, g)
+    mode, ops_term, ops_shared = h.eval_mode()
+    assert mode == hc.HC_EVAL_SHARED and ops_shared < 0.5 * ops_term
+    h.set_eval_mode(hc.HC_EVAL_PER_TERM)
+    assert h.eval_mode()[0] == hc.HC_EVAL_PER_TERM
+    h.set_eval_mode(hc.HC_EVAL_AUTO)
+    assert h.eval_mode()[0] == hc.HC_EVAL_SHARED
+    with pytest.raises(hc.HCError):
+        h.set_eval_mode(7)
+    h.free()
+    s2, _, g2 = synth.eval_throughput(2, npts=32)      # distinct monomials: per term
+    h2 = hc.system_from(s2, 2, g2)
+    assert h2.eval_mode()[0] == hc.HC_EVAL_PER_TERM
+    h2.free()
