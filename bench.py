@@ -185,12 +185,12 @@ def captured_traffic(npts: int):
 PROPOSER = os.path.join(ROOT, "paper_1109_0545_gb300", "data", "proposer_weights.npy")
 
 
-def tracker_bench(torch, hc, synth, peak_gops=None, npaths=456, cap=200, plain_sample=2):
+def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, cap=200, plain_sample=2):
     """Path steps/s and paths/s of the batched tracker (all paths in one persistent
-    kernel, FP64 LU + DD refinement; secant, quadratic, and quadratic + learned step
+    kernel, FP64 LU + DD refinement; secant, quadratic, tangent, and quadratic + learned step
     proposer) against the plain GPU tracker (all-DD elimination, secant, plain step
-    control, one path per launch).  Two families of npaths systems (456 = one wave of
-    three blocks on each of 152 SMs): the uneven-path family (n 10..64, 20..200
+    control, one path per launch).  Two families of npaths systems (608 = one wave of
+    four blocks on each of 152 SMs): the uneven-path family (n 10..64, 20..200
     monomials per polynomial, k 2..8, exponents 1..3, seed 3), whose paths all diverge,
     tracked for at most `cap` stages each (path steps/s); and its regular variant (a pure
     power and a constant per polynomial, seed 33), tracked to the end (paths/s, end
@@ -226,7 +226,8 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=456, cap=200, plain_s
     fams = {"uneven": ([synth.uneven_path_system(3, j) for j in range(npaths)], dict(max_steps=cap)),
             "uneven_regular": (reg, {})}
     variants = [("batched_secant", dict(lu_mode=hc.HC_LU_FP64_REFINE)),
-                ("batched_quadratic", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC))]
+                ("batched_quadratic", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC)),
+                ("batched_tangent", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_TANGENT))]
     if prop is not None:
         variants.append(("batched_quadratic_proposer",
                          dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC,
@@ -277,7 +278,7 @@ def paper_tables_bench(torch, hc, synth):
     (HC_TRACK_GRID); the paper's times on 8 cores of a 2011 Xeon are context.  Tables 2-3:
     n = 20, 20 monomials of degree 10 per polynomial, three systems tracked together,
     secant against quadratic predictor: successful / total corrector stages, average and
-    minimal accepted step, time."""
+    minimal accepted step, time; and the tangent (Euler) predictor beside them."""
     import numpy as np
 
     def run(systems, gammas, **kw):
@@ -313,7 +314,8 @@ def paper_tables_bench(torch, hc, synth):
     fam = [synth.paper_dim_degree(20 + j, 20, 20, 10) for j in range(3)]
     systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
     r = {"n": 20, "monomials": systems[0].nmon, "degree": 10, "systems": 3}
-    for name, pred in (("secant", hc.HC_PRED_SECANT), ("quadratic", hc.HC_PRED_QUADRATIC)):
+    for name, pred in (("secant", hc.HC_PRED_SECANT), ("quadratic", hc.HC_PRED_QUADRATIC),
+                       ("tangent", hc.HC_PRED_TANGENT)):
         st, dt = run(systems, gammas, predictor=pred)
         r[name] = summary(st, dt)
     out["tables23_dim20_deg10_qd"] = r
@@ -367,6 +369,72 @@ def common_support_bench(torch, hc, synth, peak_gops=None, npts=8192):
                      "eval_fp64_gops": gops, "eval_fp64_frac_of_measured_peak": gops / peak_gops if peak_gops else None}
     out["shared_speedup"] = out["per_term"]["eval_ms"] / out["shared"]["eval_ms"]
     sysh.free()
+    return out
+
+
+def quality_up_bench(torch, hc, synth, npaths=456):
+    """Quality up (Sec. 2): the same 456 regular-variant paths tracked in complex double,
+    double-double and quad-double (FP64 LU with refinement, quadratic predictor, corrector
+    tolerances 1e-12 / 1e-26 / 1e-58).  Quality Q = correct decimal places of the end
+    points (median over converged paths; the QD end points are the reference for double
+    and DD, the DD ones bound QD from below at its own tolerance).  The paper's quality up
+    at fixed time, y(p) = 1 + (Q_QD/Q_DD - 1)(p - 1)/(p* - 1), with p* = T_QD/T_DD the GPUs
+    that QD needs to match the time of DD on one GPU (perfect weak scaling assumed, as the
+    paper assumes optimal speedup), is reported for p = 8 GPUs."""
+    import numpy as np
+    rng = np.random.default_rng(44)
+    fam = []
+    for _ in range(npaths):
+        n = int(rng.integers(10, 65))
+        fam.append((synth.regular_system(rng, n, (20, 200), (2, 8), (1, 3), lead=1), synth.unit_complex(rng)))
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    eps = {1: 1e-12, 2: 1e-26, 4: 1e-58}
+    runs = {}
+    for L in (1, 2, 4):
+        handles = [hc.system_from(sy, L, g) for sy, g in fam]
+        x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(sy.n), L) for sy in systems])).cuda()
+        x1 = torch.zeros_like(x0)
+        o = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC,
+                                     eps=eps[L], eps_end=eps[L], eps_end_x=eps[L])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = hc.hc_track_path(handles, x0, x1, o)
+        dt = time.perf_counter() - t0
+        runs[L] = (st, hc.unpack_paths(x1.cpu().numpy(), [sy.n for sy in systems], L), dt)
+        for h in handles:
+            h.free()
+    q_st, q_end, _ = runs[4]
+
+    def digits(L):
+        st, ends, _ = runs[L]
+        d = []
+        for p in range(npaths):
+            if st[p]["status"] != hc.HC_OK or q_st[p]["status"] != hc.HC_OK:
+                continue
+            ref = q_end[p]
+            g = np.zeros_like(ref)
+            g[..., :L] = ends[p]
+            # the leading limbs of two close values subtract exactly, so the sum of the
+            # limb differences is the difference to far below its own size
+            diff = np.abs((g - ref).sum(-1)).max()
+            scale = np.abs(ref[..., 0]).max()
+            d.append(-np.log10(max(diff / scale, 1e-64)))
+        return float(np.median(d)) if d else None
+
+    out = {"paths": npaths}
+    for L, name in ((1, "double"), (2, "double_double"), (4, "quad_double")):
+        st, _, dt = runs[L]
+        out[name] = {"seconds": dt, "paths_per_s": npaths / dt, "ok_paths": sum(1 for x in st if x["status"] == hc.HC_OK)}
+    out["double"]["digits_vs_qd"] = digits(1)
+    out["double_double"]["digits_vs_qd"] = digits(2)
+    # QD's own quality: its corrector tolerance (the end game stops at 1e-58 relative)
+    q_dd = out["double_double"]["digits_vs_qd"]
+    q_qd = 58.0
+    p_star = out["quad_double"]["seconds"] / out["double_double"]["seconds"]
+    out["quad_double"]["digits"] = q_qd
+    out["qd_time_over_dd_time"] = p_star
+    if q_dd and p_star > 1.0:
+        out["quality_up_8_gpus"] = 1.0 + (q_qd / q_dd - 1.0) * (8 - 1) / (p_star - 1.0) if p_star > 8 else q_qd / q_dd
     return out
 
 
@@ -522,6 +590,7 @@ def run_gpu(args):
         extras = {"tracker": tracker_bench(torch, hc, synth, peak_gops),
                   "paper_tables": paper_tables_bench(torch, hc, synth),
                   "common_support_table1": common_support_bench(torch, hc, synth, peak_gops),
+                  "quality_up": quality_up_bench(torch, hc, synth),
                   "eval_jac_qd_points_per_s": q / (ms_qd * 1e-3),
                   "eval_jac_qd_fp64_gops": opcount.eval_ops_per_point(s, 4) * q / (ms_qd * 1e-3) / 1e9,
                   "newton_native_dd_lu_points_per_s": npts / (ms_native * 1e-3),

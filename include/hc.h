@@ -138,6 +138,10 @@ int hc_set_tiles(int rows_per_task, int blocks_per_sm);
 /* predictors (Sec. 5) and tracker execution modes */
 #define HC_PRED_SECANT 0     /* linear through the last two accepted points */
 #define HC_PRED_QUADRATIC 1  /* per coordinate, the parabola through the last three */
+#define HC_PRED_TANGENT 2    /* Euler: x + h dx/dt with dx/dt = -J^-1 dh/dt, dh/dt = f - gamma g,
+                                from the FP64 factors and the evaluation of the last Newton
+                                iteration of the last accepted stage (an FP64 direction);
+                                zeroth order on the first stage; not with HC_TRACK_GRID */
 #define HC_TRACK_PERSISTENT 0  /* one persistent kernel, paths from an atomic queue */
 #define HC_TRACK_GRAPH 1       /* one stage per launch, replayed as a CUDA graph */
 #define HC_TRACK_GRID 2        /* one path at a time on the whole GPU: each stage a CUDA
@@ -161,7 +165,7 @@ typedef struct {
     int32_t end_it;     /* Newton iterations of the end game, 8 */
     int32_t grow_after; /* consecutive successes before the step grows, 3 */
     int32_t max_steps;  /* corrector stages before HC_MAX_STEPS, 100000 */
-    int32_t predictor;  /* HC_PRED_SECANT or HC_PRED_QUADRATIC */
+    int32_t predictor;  /* HC_PRED_SECANT, HC_PRED_QUADRATIC or HC_PRED_TANGENT */
     int32_t lu_mode;    /* HC_LU_NATIVE or HC_LU_FP64_REFINE */
     int32_t max_refine; /* refinement sweeps of HC_LU_FP64_REFINE, 4 */
     int32_t mode;       /* HC_TRACK_PERSISTENT or HC_TRACK_GRAPH */

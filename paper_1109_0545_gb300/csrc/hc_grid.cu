@@ -62,7 +62,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
     __syncthreads();
     if (st.phase == 1) {
         double t1, h;
-        stage_predict<L>(a.o, st, n, a.z, a.zp, a.zpp, a.zh, a.ZP, t1, h);
+        stage_predict<L>(a.o, st, n, a.z, a.zp, a.zpp, nullptr, a.zh, a.ZP, t1, h);
         if (tid == 0) {
             g.t1 = t1;
             g.h = h;
@@ -96,7 +96,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_powers(GArgs a)
     const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
     for (int j = threadIdx.x; j < a.S.n; j += HC_TB) {
         powers_of<L>(a.S, j, a.zh, a.PW);
-        homotopy_terms<L>(a.S, j, a.zh, gs, a.HS);
+        homotopy_terms<L>(a.S, j, a.zh, gs, a.HS, false);
     }
 }
 
@@ -335,7 +335,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     const size_t o_zp = put(vec), o_zpp = put(vec), o_zh = put(vec), o_ZP = put(vec);
     const size_t o_pw = put(vec * (s->max_exp > 2 ? s->max_exp - 2 : 1));
     const size_t o_v = put(sizeof(double) * 2 * L * (vplane > 0 ? vplane : 1));
-    const size_t o_hs = put(2 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n);
+    const size_t o_hs = put(3 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n);
     const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n);
     void *ws = nullptr;
     HC_CUDA_TRY(cudaMalloc(&ws, off));

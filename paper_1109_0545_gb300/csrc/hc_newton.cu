@@ -290,7 +290,8 @@ int launch_newton(hc_system *s, int npts, double t, double *X, int lu_mode, int 
     double *PW = (double *)ws;
     double *H = (double *)(ws + pw);
     double *A = (double *)(ws + pw + hb);
-    int rc = launch_eval<L>(s->dev, npts, t, X, PW, H, A, tiles, st);
+    int rc = s->eval_shared ? launch_eval_shared<L>(s->dev, npts, t, X, PW, H, A, st)
+                            : launch_eval<L>(s->dev, npts, t, X, PW, H, A, tiles, st);
     if (rc) return rc;
     const int block = 64, grid = (npts + block - 1) / block;
     if (lu_mode == HC_LU_NATIVE) {

@@ -8,16 +8,19 @@
 
 namespace hc {
 
+// Rows r0..r1-1 of f (and J) at point p.  Every distinct monomial is evaluated for the
+// task, and the terms of rows r0..r1-1 that use it are applied (the uses of a monomial
+// are sorted by row, so they form one range, found by bisection).
 template <int L, bool JAC>
 __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool live, double t, const C<L> &gs,
-                                  double *__restrict__ F, double *__restrict__ J)
+                                  double *__restrict__ F, double *__restrict__ J, int r0, int r1)
 {
     const int n = S.n, npts = V.npts, p = V.p;
     const size_t fplane = (size_t)S.npoly * npts;
     const size_t jplane = (size_t)S.npoly * n * npts;
     // constant terms, zero Jacobian rows
     if (live)
-        for (int i = 0; i < S.npoly; i++) {
+        for (int i = r0; i < r1; i++) {
             C<L> fi = c_zero<L>();
             for (int q = __ldg(S.cptr + i); q < __ldg(S.cptr + i + 1); q++)
                 fi = c_add(fi, ld_c<L>(S.coef + (size_t)__ldg(S.cterm + q) * 2 * L, 1, 0));
@@ -56,23 +59,43 @@ __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool l
                 if (j > 0) suf = c_mul_nn(suf, V.x(pk & 0xffff));
             }
         }
-        // every term using the monomial: f_i += c value, J_{i,ij} += c a_j x^(a - e_j)
-        for (int r = __ldg(S.uuse_ptr + u); r < __ldg(S.uuse_ptr + u + 1); r++) {
+        // the uses in rows r0..r1-1: f_i += c value, J_{i,ij} += c a_j x^(a - e_j)
+        int lo = __ldg(S.uuse_ptr + u), hi = __ldg(S.uuse_ptr + u + 1);
+        for (int a = lo, b = hi; a < b;) {
+            const int mid = (a + b) >> 1;
+            if (__ldg(S.term_row + __ldg(S.uuse + mid)) < r0) a = lo = mid + 1;
+            else b = mid;
+        }
+        for (int r = lo; r < hi; r++) {
             const int m = __ldg(S.uuse + r), i = __ldg(S.term_row + m);
+            if (i >= r1) break;
             const C<L> c = ld_c<L>(S.coef + (size_t)m * 2 * L, 1, 0);
             if (!live) continue;
             const size_t fo = (size_t)i * npts + p;
             st_c<L>(F, fplane, fo, c_add(ld_c<L>(F, fplane, fo), c_mul_nn(c, value)));
-            if (JAC)
-                for (int j = 0; j < k; j++) {
-                    const size_t o = ((size_t)i * n + (__ldg(S.uvar_pack + q0 + j) & 0xffff)) * npts + p;
-                    st_c<L>(J, jplane, o, c_add(ld_c<L>(J, jplane, o), c_mul_nn(c, d[j])));
+            if (JAC) {
+                // four entries at a time: their loads are issued together (the entries of
+                // one term are distinct, but the compiler cannot know it)
+                const size_t rowo = (size_t)i * n;
+                for (int j0 = 0; j0 < k; j0 += 4) {
+                    C<L> acc[4];
+                    size_t o[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (j0 + q < k) {
+                            o[q] = (rowo + (__ldg(S.uvar_pack + q0 + j0 + q) & 0xffff)) * npts + p;
+                            acc[q] = ld_c<L>(J, jplane, o[q]);
+                        }
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (j0 + q < k) st_c<L>(J, jplane, o[q], c_add(acc[q], c_mul_nn(c, d[j0 + q])));
                 }
+            }
         }
     }
     if (t >= 0.0 && live) {
         // homotopy assembly, as in eval_rows_point
-        for (int i = 0; i < S.npoly; i++) {
+        for (int i = r0; i < r1; i++) {
             const int dg = __ldg(S.deg + i);
             const C<L> xi = V.x(i);
             const C<L> xd1 = c_pow(xi, dg - 1);
@@ -91,22 +114,26 @@ __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool l
     }
 }
 
-// persistent warps over 32-point tiles
+// persistent warps over tasks (32-point tile, group of rows), the row groups of a tile
+// consecutive
 template <int L, bool JAC>
 __global__ void __launch_bounds__(128) k_eval_shared(DevSys S, int npts, double t, const double *__restrict__ X,
                                                      const double *__restrict__ PW, double *__restrict__ F,
-                                                     double *__restrict__ J)
+                                                     double *__restrict__ J, int rows_per_task)
 {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int ntiles = (npts + 31) >> 5;
+    const int ngroups = (S.npoly + rows_per_task - 1) / rows_per_task;
     const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
-    for (int tile = warp; tile < ntiles; tile += nwarps) {
+    for (int task = warp; task < ntiles * ngroups; task += nwarps) {
+        const int tile = task / ngroups, grp = task - tile * ngroups;
         const int p = tile * 32 + lane;
         const bool live = p < npts;
         PointView<L> V{X, PW, (size_t)S.n * npts, npts, live ? p : npts - 1};
-        eval_shared_point<L, JAC>(S, V, live, t, gs, F, J);
+        const int r0 = grp * rows_per_task;
+        eval_shared_point<L, JAC>(S, V, live, t, gs, F, J, r0, min(r0 + rows_per_task, S.npoly));
     }
 }
 
@@ -128,15 +155,23 @@ int launch_eval_shared(const DevSys &S, int npts, double t, const double *X, dou
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, false>, 128, 0);
     if (occ < 1) occ = 1;
+    // row groups: enough tasks for about four warps on every SM sub-partition (each group
+    // evaluates every distinct monomial again, so no more groups than that)
+    const long long want = (long long)sms * 4 * 4;
+    long long groups = (want + ntiles - 1) / ntiles;
+    if (groups < 1) groups = 1;
+    if (groups > S.npoly) groups = S.npoly;
+    const int rpt = (int)((S.npoly + groups - 1) / groups);
+    const long long tasks = (long long)ntiles * ((S.npoly + rpt - 1) / rpt);
     long long grid = (long long)sms * occ;
-    const long long need = (ntiles + 3) / 4;
+    const long long need = (tasks + 3) / 4;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     hc_prof_mark(st, true);
     if (J)
-        k_eval_shared<L, true><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J);
+        k_eval_shared<L, true><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
     else
-        k_eval_shared<L, false><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J);
+        k_eval_shared<L, false><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
     hc_prof_mark(st, false);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return hc_cuda_fail(e, "k_eval_shared launch");

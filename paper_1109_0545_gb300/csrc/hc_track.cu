@@ -18,7 +18,7 @@
 namespace hc {
 
 struct SlotLayout {
-    size_t pw, v, hs, h, jh, b, dz, zp, stride;
+    size_t pw, v, hs, ht, h, jh, b, dz, zp, stride;
 };
 
 struct TrackArgs {
@@ -26,7 +26,8 @@ struct TrackArgs {
     const long long *xoff;    // [npaths] offset (doubles) of path p in x0/x1
     const double *x0;
     double *x1;
-    double *vecs;             // per path: previous, second previous, predicted+corrected
+    double *vecs;             // per path: previous, second previous, predicted+corrected,
+                              // tangent (each 2 L n doubles)
     PathState *st;
     hc_track_opts o;
     char *slots;
@@ -54,6 +55,7 @@ template <int L> __device__ __forceinline__ Slot<L> slot_of(const TrackArgs &a, 
     w.PW = (double *)(base + a.lay.pw);
     w.V = (double *)(base + a.lay.v);
     w.HS = (double *)(base + a.lay.hs);
+    w.HT = a.o.predictor == HC_PRED_TANGENT ? (double *)(base + a.lay.ht) : nullptr;
     w.H = (double *)(base + a.lay.h);
     w.JH = (double *)(base + a.lay.jh);
     w.DZ = (double *)(base + a.lay.dz);
@@ -78,9 +80,11 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
     const hc_track_opts &o = a.o;
     const int n = S.n, tid = threadIdx.x;
     double *z = a.x1 + a.xoff[p];
-    double *zp = a.vecs + 3 * a.xoff[p];
+    double *zp = a.vecs + 4 * a.xoff[p];
     double *zpp = zp + 2 * L * n;
     double *zh = zpp + 2 * L * n;
+    double *tv = zh + 2 * L * n;  // [2][n] dx/dt at the last accepted point (tangent predictor)
+    const bool tangent = o.predictor == HC_PRED_TANGENT;
     PathState st = a.st[p];
     if (st.phase == 3) return;
     if (st.phase == 0) {
@@ -92,7 +96,7 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
     int stages = 0;
     while (st.phase == 1 && stages < max_stages) {
         double t1, h;
-        stage_predict<L>(o, st, n, z, zp, zpp, zh, w.ZP, t1, h);
+        stage_predict<L>(o, st, n, z, zp, zpp, tv, zh, w.ZP, t1, h);
         // corrector: Alg. 4.1
         double res = 1.0, res_first = -1.0, cond = 0.0;
         int it = 0, nst = HC_OK, conv = 0;
@@ -106,8 +110,19 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
             if (nst != HC_OK) break;
             conv = (res <= o.eps) || (no.dzn <= o.eps_x * (no.zn > 1.0 ? no.zn : 1.0));
         }
+        // tangent at the corrected point: dx/dt = -J^-1 dh/dt from the last iteration's
+        // evaluation and FP64 factors, kept if the stage is accepted
+        if (tangent && conv && nst == HC_OK) {
+            if (tid < 32) warp_lu64_solve(n, w.B, w.PIV, w.HT, w.Y);
+            __syncthreads();
+        }
+        const long long succ0 = st.n_succ;
         stage_finish<L>(o, st, sh, n, z, zp, zpp, zh, w.ZP, t1, h, it, nst, conv, res, res_first, cond,
                         log, a.log_cap);
+        if (tangent && st.n_succ > succ0) {
+            for (int q = tid; q < 2 * n; q += HC_TB) tv[q] = -w.Y[q];
+            __syncthreads();
+        }
         stages++;
     }
     if (st.phase == 2) {
@@ -137,7 +152,7 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
 }
 
 template <int L>
-__global__ void __launch_bounds__(HC_TB, 3) k_track(TrackArgs a, int persistent)
+__global__ void __launch_bounds__(HC_TB, L == 4 ? 3 : 4) k_track(TrackArgs a, int persistent)
 {
     __shared__ BlockShared sh;
     __shared__ int s_p;
@@ -202,8 +217,10 @@ static int check_opts(const hc_track_opts *o)
         return hc_fail(HC_EINVAL, "need grow >= 1 and 0 < shrink < 1");
     if (o->max_it < 1 || o->end_it < 0 || o->grow_after < 1 || o->max_steps < 1)
         return hc_fail(HC_EINVAL, "need max_it >= 1, end_it >= 0, grow_after >= 1, max_steps >= 1");
-    if (o->predictor != HC_PRED_SECANT && o->predictor != HC_PRED_QUADRATIC)
+    if (o->predictor != HC_PRED_SECANT && o->predictor != HC_PRED_QUADRATIC && o->predictor != HC_PRED_TANGENT)
         return hc_fail(HC_EINVAL, "unknown predictor %d", o->predictor);
+    if (o->predictor == HC_PRED_TANGENT && (o->lu_mode != HC_LU_FP64_REFINE || o->mode == HC_TRACK_GRID))
+        return hc_fail(HC_EINVAL, "the tangent predictor needs HC_LU_FP64_REFINE and a block mode");
     if (o->lu_mode != HC_LU_NATIVE && o->lu_mode != HC_LU_FP64_REFINE)
         return hc_fail(HC_EINVAL, "unknown lu_mode %d", o->lu_mode);
     if (o->lu_mode == HC_LU_FP64_REFINE && (o->max_refine < 1 || o->max_refine > 64))
@@ -281,9 +298,13 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         return HC_SUCCESS;
     }
     const int sms = hc_num_sms();
-    // the FP64 factors go to shared memory when a block's share stays within 72 KiB (three
-    // blocks per SM, the register limit, then still fit in the SM's 228 KiB)
-    const int b_smem = sizeof(double) * track_smem_doubles(nmax, 1) <= 72 * 1024;
+    // the FP64 factors go to shared memory when a block's share stays within what the
+    // register limit's blocks per SM leave of the SM's 228 KiB: four blocks (128 registers)
+    // for double and DD, 54 KiB each; three for QD (168 registers), 72 KiB each.  With four
+    // blocks and the factors in global memory the tracker still runs 8 % more stages per
+    // second than with three and the factors in shared memory (uneven family, n <= 64).
+    const size_t smem_cap = L == 4 ? 72 * 1024 : 54 * 1024;
+    const int b_smem = sizeof(double) * track_smem_doubles(nmax, 1) <= smem_cap;
     const size_t smem = sizeof(double) * track_smem_doubles(nmax, b_smem);
     int occ = L == 1 ? occupancy_track<1>(smem) : L == 2 ? occupancy_track<2>(smem) : occupancy_track<4>(smem);
     const int grid = (int)(npaths < (long long)sms * occ ? npaths : (long long)sms * occ);
@@ -293,7 +314,8 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     auto put = [&](size_t bytes) { size_t at = o; o = hc_align256(o + bytes); return at; };
     lay.pw = put(sizeof(double) * 2 * L * (size_t)nmax * (emax > 2 ? emax - 2 : 1));
     lay.v = put(sizeof(double) * 2 * L * (size_t)(vmax > 0 ? vmax : 1));
-    lay.hs = put(sizeof(double) * 2 * L * 2 * (size_t)nmax);
+    lay.hs = put(sizeof(double) * 2 * L * 3 * (size_t)nmax);
+    lay.ht = put(sizeof(double) * 2 * (size_t)nmax);
     lay.h = put(sizeof(double) * 2 * L * (size_t)nmax);
     lay.jh = put(sizeof(double) * 2 * L * (size_t)nmax * nmax);
     lay.b = put(b_smem ? 0 : sizeof(double) * 2 * (size_t)nmax * nmax);
@@ -303,7 +325,7 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
 
     size_t b_sys = hc_align256(sizeof(DevSys) * npaths);
     size_t b_off = hc_align256(sizeof(long long) * npaths);
-    size_t b_vec = hc_align256(sizeof(double) * 3 * (size_t)total);
+    size_t b_vec = hc_align256(sizeof(double) * 4 * (size_t)total);
     size_t b_st = hc_align256(sizeof(PathState) * npaths);
     size_t b_ctr = 256;
     size_t bytes = b_sys + b_off + b_vec + b_st + b_ctr + lay.stride * (size_t)grid;

@@ -14,8 +14,9 @@ namespace hc {
 template <int L> struct Slot {
     double *PW;    // [max_exp-2][2][L][n]
     double *V;     // [2][L][nvar+nmon] (plane = nvar+nmon): partials, then values
-    double *HS;    // [2][L][2n] start-system terms of the homotopy per row: gamma (1-t)
-                   // (x_i^d_i - 1), then gamma (1-t) d_i x_i^(d_i - 1)
+    double *HS;    // [2][L][3n] start-system terms of the homotopy per row: gamma (1-t)
+                   // (x_i^d_i - 1), gamma (1-t) d_i x_i^(d_i - 1), gamma (x_i^d_i - 1)
+    double *HT;    // [2][n] leading limbs of dh/dt = f - gamma g, or NULL (not needed)
     double *H;     // [2][L][n]
     double *JH;    // [2][L][n][n]
     double *B;     // [2][n][n] FP64 factors
@@ -169,18 +170,20 @@ __device__ __forceinline__ void powers_of(const DevSys &S, int j, const double *
 }
 
 // Start-system terms of row i of the homotopy at (z, t), t >= 0: gamma (1-t) (x_i^d - 1)
-// into HS[i] and gamma (1-t) d x_i^(d-1) into HS[n + i] (d = deg f_i), gs = gamma (1-t).
+// into HS[i], gamma (1-t) d x_i^(d-1) into HS[n + i] (d = deg f_i), gs = gamma (1-t); with
+// tangent, also gamma (x_i^d - 1) into HS[2n + i] (for dh/dt).
 template <int L>
 __device__ __forceinline__ void homotopy_terms(const DevSys &S, int i, const double *__restrict__ z,
-                                               const C<L> &gs, double *__restrict__ HS)
+                                               const C<L> &gs, double *__restrict__ HS, bool tangent)
 {
     const int n = S.n, d = __ldg(S.deg + i);
     const C<L> xi = ld_c<L>(z, n, i);
     const C<L> xd1 = c_pow(xi, d - 1);
     C<L> g = c_mul(xd1, xi);
     g.re = r_sub(g.re, r_from<L>(1.0));
-    st_c<L>(HS, 2 * n, i, c_mul(gs, g));
-    st_c<L>(HS, 2 * n, n + i, c_mul(gs, c_scale_int(xd1, d)));
+    st_c<L>(HS, 3 * n, i, c_mul(gs, g));
+    st_c<L>(HS, 3 * n, n + i, c_mul(gs, c_scale_int(xd1, d)));
+    if (tangent) st_c<L>(HS, 3 * n, 2 * n + i, c_mul(c_from<L>(S.gre, S.gim), g));
 }
 
 // Phase 2 for one entry e = i (n+1) + j: the sum of its contributions in the original
@@ -188,7 +191,7 @@ __device__ __forceinline__ void homotopy_terms(const DevSys &S, int i, const dou
 template <int L>
 __device__ __forceinline__ void entry_from_V(const DevSys &S, int e, double t, const double *__restrict__ V,
                                              const double *__restrict__ HS, double *__restrict__ H,
-                                             double *__restrict__ JH)
+                                             double *__restrict__ JH, double *__restrict__ HT = nullptr)
 {
     const int n = S.n;
     const size_t vplane = (size_t)S.nvar + S.nmon;
@@ -201,10 +204,16 @@ __device__ __forceinline__ void entry_from_V(const DevSys &S, int e, double t, c
     for (int r = __ldg(S.tptr + e); r < r1; r++) acc = c_add(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
     if (t >= 0.0) {
         if (j == n) {
-            acc = c_add(ld_c<L>(HS, 2 * n, i), c_mul_d(acc, t));
+            if (HT) {
+                // dh_i/dt = f_i - gamma g_i, leading limbs
+                const C<L> dt = c_sub(acc, ld_c<L>(HS, 3 * n, 2 * n + i));
+                HT[i] = dt.re.v[0];
+                HT[n + i] = dt.im.v[0];
+            }
+            acc = c_add(ld_c<L>(HS, 3 * n, i), c_mul_d(acc, t));
         } else {
             acc = c_mul_d(acc, t);
-            if (i == j) acc = c_add(acc, ld_c<L>(HS, 2 * n, n + i));
+            if (i == j) acc = c_add(acc, ld_c<L>(HS, 3 * n, n + i));
         }
     }
     if (j == n)
@@ -222,13 +231,13 @@ __device__ void block_eval(const DevSys &S, const double *__restrict__ z, double
     const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
     for (int j = tid; j < n; j += HC_TB) {
         powers_of<L>(S, j, z, w.PW);
-        if (t >= 0.0 && j < S.npoly) homotopy_terms<L>(S, j, z, gs, w.HS);
+        if (t >= 0.0 && j < S.npoly) homotopy_terms<L>(S, j, z, gs, w.HS, w.HT != nullptr);
     }
     __syncthreads();
     for (int q = tid; q < S.nmon; q += HC_TB) monomial_to_V<L>(S, __ldg(S.perm + q), z, w.PW, w.V);
     __syncthreads();
     const int ne = S.npoly * (n + 1);
-    for (int q = tid; q < ne; q += HC_TB) entry_from_V<L>(S, __ldg(S.eperm + q), t, w.V, w.HS, w.H, w.JH);
+    for (int q = tid; q < ne; q += HC_TB) entry_from_V<L>(S, __ldg(S.eperm + q), t, w.V, w.HS, w.H, w.JH, w.HT);
     __syncthreads();
 }
 

@@ -88,8 +88,8 @@ __device__ __forceinline__ void path_init(PathState &st, const hc_track_opts &o,
 // writes the predicted point into zh and its copy ZP; block-level, ends synchronised.
 template <int L>
 __device__ void stage_predict(const hc_track_opts &o, const PathState &st, int n, const double *z,
-                              const double *zp, const double *zpp, double *zh, double *ZP, double &t1_out,
-                              double &h_out)
+                              const double *zp, const double *zpp, const double *tv, double *zh, double *ZP,
+                              double &t1_out, double &h_out)
 {
     const int tid = threadIdx.x;
     double t1 = add_(st.t, st.lambda);
@@ -99,7 +99,14 @@ __device__ void stage_predict(const hc_track_opts &o, const PathState &st, int n
     h_out = h;
     double *const wzp = ZP;
         // predictor (Alg. 3.1 "predict"; Sec. 5 for the quadratic one)
-        if (o.predictor == HC_PRED_QUADRATIC && st.nhist >= 3) {
+        if (o.predictor == HC_PRED_TANGENT && tv && st.nhist >= 2) {
+            // tv[2][n] = dx/dt at the last accepted point (FP64)
+            for (int j = tid; j < n; j += HC_TB) {
+                const C<L> v = c_add(ld_c<L>(z, n, j), c_from<L>(mul_(h, tv[j]), mul_(h, tv[n + j])));
+                st_c<L>(zh, n, j, v);
+                st_c<L>(wzp, n, j, v);
+            }
+        } else if (o.predictor == HC_PRED_QUADRATIC && st.nhist >= 3) {
             const double w0 = __ddiv_rn(mul_(sub_(t1, st.tp), sub_(t1, st.t)), mul_(sub_(st.tpp, st.tp), sub_(st.tpp, st.t)));
             const double w1 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.t)), mul_(sub_(st.tp, st.tpp), sub_(st.tp, st.t)));
             const double w2 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.tp)), mul_(sub_(st.t, st.tpp), sub_(st.t, st.tp)));

@@ -52,7 +52,7 @@ class PathStats(ct.Structure):
 STEP_RECORD_DTYPE = np.dtype([("t", "f8"), ("lam", "f8"), ("res_first", "f8"), ("res_last", "f8"),
                               ("pc_dist", "f8"), ("cond_log10", "f8"), ("iters", "i4"),
                               ("accepted", "i4")])
-HC_PRED_SECANT, HC_PRED_QUADRATIC = 0, 1
+HC_PRED_SECANT, HC_PRED_QUADRATIC, HC_PRED_TANGENT = 0, 1, 2
 HC_EVAL_AUTO, HC_EVAL_PER_TERM, HC_EVAL_SHARED = 0, 1, 2
 HC_TRACK_PERSISTENT, HC_TRACK_GRAPH, HC_TRACK_GRID = 0, 1, 2
 

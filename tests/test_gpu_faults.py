@@ -55,7 +55,10 @@ def test_invalid_options_are_rejected_before_any_launch():
     x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(3), 2)])).cuda()
     x1 = torch.zeros_like(x0)
     for bad in (dict(lambda0=-1.0), dict(shrink=1.5), dict(max_it=0), dict(predictor=7),
-                dict(mode=9), dict(mode=hc.HC_TRACK_GRID, lu_mode=hc.HC_LU_NATIVE)):
+                dict(mode=9), dict(mode=hc.HC_TRACK_GRID, lu_mode=hc.HC_LU_NATIVE),
+                dict(predictor=hc.HC_PRED_TANGENT, lu_mode=hc.HC_LU_NATIVE),
+                dict(predictor=hc.HC_PRED_TANGENT, lu_mode=hc.HC_LU_FP64_REFINE, mode=hc.HC_TRACK_GRID),
+                dict(explore=-1.0)):
         with pytest.raises(hc.HCError) as e:
             hc.hc_track_path(handles, x0, x1, hc.hc_track_opts_default(**bad))
         assert e.value.code == hc.HC_EINVAL

@@ -202,3 +202,28 @@ def test_exploration_perturbs_steps_reproducibly_and_the_oracle_replays_them():
         assert fail == -1 and status == 0
         assert rel_err_per_point(ends[p][None], x1[None])[0] <= TOL[2]
     assert off_lattice > 0
+
+
+def test_tangent_predictor_reaches_the_oracle_end_points():
+    """The Euler (tangent) predictor: every path ends at the oracle's end point (the oracle
+    tracks with the secant predictor; same gamma, same start root, so the same root), in
+    fewer corrector stages than the secant predictor, and the persistent and graph-stepped
+    modes agree bit for bit."""
+    torch = torch_cuda()
+    fam = regular_family(480, 6, 4)
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    sec = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE)
+    tan = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_TANGENT)
+    s_st, _, _ = gpu_track(torch, systems, gammas, 2, sec)
+    t_st, t_end, _ = gpu_track(torch, systems, gammas, 2, tan)
+    assert compare_with_oracle(systems, gammas, 2, sec, t_st, t_end, strict_counts=False) == len(systems)
+    n_sec = np.mean([x["n_corr"] for x in s_st])
+    n_tan = np.mean([x["n_corr"] for x in t_st])
+    print(f"secant {n_sec:.1f}, tangent {n_tan:.1f} stages per path")
+    assert n_tan < n_sec
+    g_st, g_end, _ = gpu_track(torch, systems, gammas, 2,
+                               hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_TANGENT,
+                                                        mode=hc.HC_TRACK_GRAPH, graph_steps=3))
+    for a, b, x, y in zip(t_st, g_st, t_end, g_end):
+        assert (a["n_succ"], a["n_corr"], a["status"]) == (b["n_succ"], b["n_corr"], b["status"])
+        assert np.array_equal(x, y)
