@@ -11,6 +11,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "track.cuh"
@@ -34,6 +35,8 @@ struct TrackArgs {
     SlotLayout lay;
     int *queue;
     int *active;
+    const int *order;         // [npaths] paths in the order they are taken: largest
+                              // evaluation cost first, so the last ones to start are short
     hc_step_record *log;
     int log_cap;
     int npaths;
@@ -162,13 +165,13 @@ __global__ void __launch_bounds__(HC_TB, L == 4 ? 3 : 4) k_track(TrackArgs a, in
         for (;;) {
             if (threadIdx.x == 0) s_p = atomicAdd(a.queue, 1);
             __syncthreads();
-            const int p = s_p;
+            const int q = s_p;
             __syncthreads();
-            if (p >= a.npaths) break;
-            path_run<L>(a, p, w, sh, 0x7fffffff);
+            if (q >= a.npaths) break;
+            path_run<L>(a, a.order[q], w, sh, 0x7fffffff);
         }
     } else {
-        for (int p = blockIdx.x; p < a.npaths; p += gridDim.x) path_run<L>(a, p, w, sh, 1);
+        for (int q = blockIdx.x; q < a.npaths; q += gridDim.x) path_run<L>(a, a.order[q], w, sh, 1);
     }
 }
 
@@ -327,8 +330,9 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     size_t b_off = hc_align256(sizeof(long long) * npaths);
     size_t b_vec = hc_align256(sizeof(double) * 4 * (size_t)total);
     size_t b_st = hc_align256(sizeof(PathState) * npaths);
+    size_t b_ord = hc_align256(sizeof(int) * npaths);
     size_t b_ctr = 256;
-    size_t bytes = b_sys + b_off + b_vec + b_st + b_ctr + lay.stride * (size_t)grid;
+    size_t bytes = b_sys + b_off + b_vec + b_st + b_ord + b_ctr + lay.stride * (size_t)grid;
     DevBuf ws;
     HC_CUDA_TRY(cudaMalloc(&ws.p, bytes));
     char *b = (char *)ws.p;
@@ -338,10 +342,12 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     a.xoff = (const long long *)(b + b_sys);
     a.vecs = (double *)(b + b_sys + b_off);
     a.st = (PathState *)(b + b_sys + b_off + b_vec);
-    int *ctr = (int *)(b + b_sys + b_off + b_vec + b_st);
+    int *ord = (int *)(b + b_sys + b_off + b_vec + b_st);
+    int *ctr = (int *)(b + b_sys + b_off + b_vec + b_st + b_ord);
     a.queue = ctr;
     a.active = ctr + 1;
-    a.slots = b + b_sys + b_off + b_vec + b_st + b_ctr;
+    a.order = ord;
+    a.slots = b + b_sys + b_off + b_vec + b_st + b_ord + b_ctr;
     a.lay = lay;
     a.x0 = x0;
     a.x1 = x1;
@@ -354,6 +360,16 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.sys, hs.data(), sizeof(DevSys) * npaths, cudaMemcpyHostToDevice, st));
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.xoff, off.data(), sizeof(long long) * npaths, cudaMemcpyHostToDevice, st));
     HC_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(PathState) * npaths, st));
+    // largest first: FP64 instructions of one evaluation plus the LU (a per-stage cost; the
+    // number of stages is not known in advance)
+    std::vector<int> horder((size_t)npaths);
+    std::vector<double> cost((size_t)npaths);
+    for (int p = 0; p < npaths; p++) {
+        horder[p] = p;
+        cost[p] = sys[p]->ops_term + 4.0 / 3.0 * (double)sys[p]->n * sys[p]->n * sys[p]->n;
+    }
+    std::stable_sort(horder.begin(), horder.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    HC_CUDA_TRY(cudaMemcpyAsync(ord, horder.data(), sizeof(int) * npaths, cudaMemcpyHostToDevice, st));
     int hctr[2] = {0, npaths};
     HC_CUDA_TRY(cudaMemcpyAsync(ctr, hctr, sizeof hctr, cudaMemcpyHostToDevice, st));
 
