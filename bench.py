@@ -185,16 +185,16 @@ def captured_traffic(npts: int):
 PROPOSER = os.path.join(ROOT, "paper_1109_0545_gb300", "data", "proposer_weights.npy")
 
 
-def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, cap=200, plain_sample=2):
+def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=2432, cap=200, plain_sample=2):
     """Path steps/s and paths/s of the batched tracker (all paths in one persistent
     kernel, FP64 LU + DD refinement; secant, quadratic, tangent, and quadratic + learned step
     proposer) against the plain GPU tracker (all-DD elimination, secant, plain step
-    control, one path per launch).  Two families of npaths systems (608 = one wave of
-    four blocks on each of 152 SMs): the uneven-path family (n 10..64, 20..200
-    monomials per polynomial, k 2..8, exponents 1..3, seed 3), whose paths all diverge,
+    control, one path per launch).  Two families: the uneven-path family (n 10..64,
+    20..200 monomials per polynomial, k 2..8, exponents 1..3, seed 3; uneven_paths = 2432
+    systems, four waves of four blocks on each of 152 SMs), whose paths all diverge,
     tracked for at most `cap` stages each (path steps/s); and its regular variant (a pure
-    power and a constant per polynomial, seed 33), tracked to the end (paths/s, end
-    points compared with the batched all-DD tracker's at 1e-28).  FP64 throughput: the
+    power and a constant per polynomial, seed 33; npaths = 608, one wave), tracked to the
+    end (paths/s, end points compared with the batched all-DD tracker's at 1e-28).  FP64 throughput: the
     Newton iterations of all paths (end game included) times the FP64 instructions of one
     iteration without its refinement sweeps (`opcount.newton_iteration_ops`, a lower bound)
     per second, against the measured FP64 peak."""
@@ -223,7 +223,7 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, cap=200, plain_s
         n = int(rng.integers(10, 65))
         reg.append((synth.regular_system(rng, n, (20, 200), (2, 8), (1, 3), lead=1),
                     synth.unit_complex(rng)))
-    fams = {"uneven": ([synth.uneven_path_system(3, j) for j in range(npaths)], dict(max_steps=cap)),
+    fams = {"uneven": ([synth.uneven_path_system(3, j) for j in range(uneven_paths)], dict(max_steps=cap)),
             "uneven_regular": (reg, {})}
     variants = [("batched_secant", dict(lu_mode=hc.HC_LU_FP64_REFINE)),
                 ("batched_quadratic", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC)),
@@ -235,6 +235,7 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, cap=200, plain_s
     out = {}
     for name, (fam, extra) in fams.items():
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+        npaths = len(systems)
         it_ops = [opcount.newton_iteration_ops(sy, 2) for sy in systems]
         plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE, **extra)
         p_steps, p_dt = 0, 0.0

@@ -24,6 +24,10 @@
 
 #include "track.cuh"
 
+#include <vector>
+
+#define HC_GCHUNK 32  // contributions per chunk of an entry's sum
+
 namespace hc {
 
 struct GStage {
@@ -38,6 +42,13 @@ struct GArgs {
     const double *x0;
     double *z, *zp, *zpp, *zh, *ZP, *PW, *V, *HS, *H, *JH, *B, *RV, *DZ;
     int32_t *PIV;
+    // the entries' contribution lists cut into chunks of at most HC_GCHUNK, summed in
+    // parallel (k_g_chunks), then per entry in chunk order (k_g_entries)
+    const int32_t *cbeg;      // [nchunks+1] chunk c covers tlist[cbeg[c] .. cend[c])
+    const int32_t *cend;
+    const int32_t *eptr;      // [ne+1] the chunks of entry e: eptr[e] .. eptr[e+1]-1
+    double *P;                // [2][L][nchunks] chunk sums
+    int nchunks;
     hc_track_opts o;
     hc_step_record *log;
     int log_cap;
@@ -107,6 +118,17 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_monomials(GArgs a)
     if (q < a.S.nmon) monomial_to_V<L>(a.S, __ldg(a.S.perm + q), a.zh, a.PW, a.V);
 }
 
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_chunks(GArgs a)
+{
+    const GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int c = blockIdx.x * HC_TB + threadIdx.x;
+    if (c >= a.nchunks) return;
+    st_c<L>(a.P, a.nchunks, c, sum_contributions<L>(a.S, __ldg(a.cbeg + c), __ldg(a.cend + c), a.V));
+}
+
+// the chunk sums of each entry added in chunk order (an entry of one chunk takes its sum
+// as is, the same value as one sequential sum), then the homotopy
 template <int L> __global__ void __launch_bounds__(HC_TB) k_g_entries(GArgs a)
 {
     const GStage &g = *a.g;
@@ -114,14 +136,18 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_entries(GArgs a)
     const int q = blockIdx.x * HC_TB + threadIdx.x;
     const int ne = a.S.npoly * (a.S.n + 1);
     if (q >= ne) return;
-    entry_from_V<L>(a.S, __ldg(a.S.eperm + q), g.t1, a.V, a.HS, a.H, a.JH);
+    const int e = __ldg(a.S.eperm + q);
+    const int c0 = __ldg(a.eptr + e), c1 = __ldg(a.eptr + e + 1);
+    C<L> acc = ld_c<L>(a.P, a.nchunks, c0);
+    for (int c = c0 + 1; c < c1; c++) acc = c_add(acc, ld_c<L>(a.P, a.nchunks, c));
+    entry_finish<L>(a.S, e, g.t1, acc, a.HS, a.H, a.JH, nullptr);
 }
 
 // residual of the incoming point, FP64 LU, first solve (block_newton's first half)
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a)
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a, int b_smem)
 {
     __shared__ BlockShared sh;
-    extern __shared__ double ysh[];  // [2][n]
+    extern __shared__ double ysh[];  // [2][n], then (b_smem) the factors [2][n][n]
     GStage &g = *a.g;
     if (!g_active(g)) return;
     const int n = a.S.n, tid = threadIdx.x;
@@ -137,7 +163,12 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a)
     fin = block_and(fin, sh);
     const double res = sqrt(block_max(r2, sh));
     double cond = 0.0;
-    int status = fin ? block_lu64<L>(n, a.JH, a.B, a.PIV, sh, &cond) : HC_NONFINITE;
+    double *Bf = b_smem ? ysh + 2 * n : a.B;
+    int status = fin ? block_lu64<L>(n, a.JH, Bf, a.PIV, sh, &cond) : HC_NONFINITE;
+    if (status == HC_OK && b_smem) {
+        // the factors for the refinement solves of the later kernels
+        for (int q = tid; q < 2 * n * n; q += HC_TB) a.B[q] = Bf[q];
+    }
     if (status == HC_OK) {
         for (int i = tid; i < n; i += HC_TB) {
             double re, im;
@@ -146,7 +177,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a)
             a.RV[n + i] = -im;
         }
         __syncthreads();
-        if (tid < 32) warp_lu64_solve(n, a.B, a.PIV, a.RV, ysh);
+        if (tid < 32) warp_lu64_solve(n, Bf, a.PIV, a.RV, ysh);
         __syncthreads();
         double xn = 0.0;
         for (int i = tid; i < n; i += HC_TB) {
@@ -295,6 +326,14 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
     const int mblocks = (a.S.nmon + HC_TB - 1) / HC_TB;
     const int eblocks = (a.S.npoly * (a.S.n + 1) + HC_TB - 1) / HC_TB;
     const size_t ysh_bytes = sizeof(double) * 2 * (size_t)a.S.n;  // n <= 256: at most 4 KiB
+    // the FP64 LU in shared memory when the factors fit (n <= 110)
+    const size_t bsm = sizeof(double) * 2 * (size_t)a.S.n * a.S.n;
+    const int b_smem = ysh_bytes + bsm <= 200 * 1024;
+    const size_t fac_bytes = ysh_bytes + (b_smem ? bsm : 0);
+    if (fac_bytes > 48 * 1024) {
+        cudaError_t ea = cudaFuncSetAttribute(k_g_factor<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fac_bytes);
+        if (ea != cudaSuccess) return hc_cuda_fail(ea, "k_g_factor shared memory");
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return hc_cuda_fail(e, "cudaStreamBeginCapture");
@@ -302,8 +341,9 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
     for (int it = 0; it < max_it; it++) {
         k_g_powers<L><<<1, HC_TB, 0, cs>>>(a);
         k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_TB, 0, cs>>>(a);
+        k_g_chunks<L><<<(a.nchunks + HC_TB - 1) / HC_TB, HC_TB, 0, cs>>>(a);
         k_g_entries<L><<<eblocks, HC_TB, 0, cs>>>(a);
-        k_g_factor<L><<<1, HC_TB, ysh_bytes, cs>>>(a);
+        k_g_factor<L><<<1, HC_TB, fac_bytes, cs>>>(a, b_smem);
         for (int r = 0; r < max_refine; r++) {
             k_g_refine_rows<L><<<a.S.n, 32, 0, cs>>>(a);
             k_g_refine_solve<L><<<1, HC_TB, ysh_bytes, cs>>>(a);
@@ -337,6 +377,23 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     const size_t o_v = put(sizeof(double) * 2 * L * (vplane > 0 ? vplane : 1));
     const size_t o_hs = put(3 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n);
     const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n);
+    // chunks of the entries' contribution lists (from the transpose table's offsets)
+    const int ne = s->npoly * (n + 1);
+    std::vector<int32_t> tptr((size_t)ne + 1), cbeg, cend, eptr((size_t)ne + 1, 0);
+    HC_CUDA_TRY(cudaMemcpy(tptr.data(), s->dev.tptr, sizeof(int32_t) * (ne + 1), cudaMemcpyDeviceToHost));
+    for (int e = 0; e < ne; e++) {
+        int r = tptr[e];
+        do {
+            const int r1 = r + HC_GCHUNK < tptr[e + 1] ? r + HC_GCHUNK : tptr[e + 1];
+            cbeg.push_back(r);
+            cend.push_back(r1);
+            r = r1;
+        } while (r < tptr[e + 1]);
+        eptr[e + 1] = (int32_t)cbeg.size();
+    }
+    const int nchunks = (int)cbeg.size();
+    const size_t o_cb = put(sizeof(int32_t) * nchunks), o_ce = put(sizeof(int32_t) * nchunks),
+                 o_ep = put(sizeof(int32_t) * (ne + 1)), o_p = put(sizeof(double) * 2 * L * (size_t)nchunks);
     void *ws = nullptr;
     HC_CUDA_TRY(cudaMalloc(&ws, off));
     char *b = (char *)ws;
@@ -359,6 +416,11 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     a.RV = (double *)(b + o_rv);
     a.DZ = (double *)(b + o_dz);
     a.PIV = (int32_t *)(b + o_piv);
+    a.cbeg = (const int32_t *)(b + o_cb);
+    a.cend = (const int32_t *)(b + o_ce);
+    a.eptr = (const int32_t *)(b + o_ep);
+    a.P = (double *)(b + o_p);
+    a.nchunks = nchunks;
     a.o = *o;
     a.log = log;
     a.log_cap = log_cap;
@@ -369,6 +431,9 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, off, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_cb, cbeg.data(), sizeof(int32_t) * nchunks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_ce, cend.data(), sizeof(int32_t) * nchunks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_ep, eptr.data(), sizeof(int32_t) * (ne + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(ready, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
     if (e != cudaSuccess) rc = hc_cuda_fail(e, "grid tracker set-up");

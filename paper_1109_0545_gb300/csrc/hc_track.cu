@@ -360,8 +360,11 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.sys, hs.data(), sizeof(DevSys) * npaths, cudaMemcpyHostToDevice, st));
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.xoff, off.data(), sizeof(long long) * npaths, cudaMemcpyHostToDevice, st));
     HC_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(PathState) * npaths, st));
-    // largest first: FP64 instructions of one evaluation plus the LU (a per-stage cost; the
-    // number of stages is not known in advance)
+    // largest first by the cost of a stage (FP64 instructions of one evaluation plus the LU;
+    // the number of stages is not known in advance), so the last paths to start are short.
+    // The first wave (one path per resident block) is then shuffled: the block scheduler
+    // places consecutive blocks on the same SM, and the largest paths in consecutive
+    // blocks would share SMs (measured: 21 % fewer stages per second for 608 paths).
     std::vector<int> horder((size_t)npaths);
     std::vector<double> cost((size_t)npaths);
     for (int p = 0; p < npaths; p++) {
@@ -369,6 +372,21 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         cost[p] = sys[p]->ops_term + 4.0 / 3.0 * (double)sys[p]->n * sys[p]->n * sys[p]->n;
     }
     std::stable_sort(horder.begin(), horder.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    {
+        // Fisher-Yates over the first wave with a fixed SplitMix64 stream (deterministic)
+        unsigned long long x = 0x5eedULL;
+        const int wave = npaths < grid ? npaths : grid;
+        for (int q = wave - 1; q > 0; q--) {
+            unsigned long long z = (x += 0x9e3779b97f4a7c15ULL);
+            z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+            z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+            z ^= z >> 31;
+            const int r = (int)(z % (unsigned long long)(q + 1));
+            const int t0 = horder[q];
+            horder[q] = horder[r];
+            horder[r] = t0;
+        }
+    }
     HC_CUDA_TRY(cudaMemcpyAsync(ord, horder.data(), sizeof(int) * npaths, cudaMemcpyHostToDevice, st));
     int hctr[2] = {0, npaths};
     HC_CUDA_TRY(cudaMemcpyAsync(ctr, hctr, sizeof hctr, cudaMemcpyHostToDevice, st));

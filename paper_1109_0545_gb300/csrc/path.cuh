@@ -186,22 +186,14 @@ __device__ __forceinline__ void homotopy_terms(const DevSys &S, int i, const dou
     if (tangent) st_c<L>(HS, 3 * n, 2 * n + i, c_mul(c_from<L>(S.gre, S.gim), g));
 }
 
-// Phase 2 for one entry e = i (n+1) + j: the sum of its contributions in the original
-// monomial order, then the homotopy (t >= 0); j == n is h_i, else dh_i/dx_j.
+// The homotopy (t >= 0) on the sum acc of entry e = i (n+1) + j, and its store: j == n is
+// h_i (and, with HT, dh_i/dt), else dh_i/dx_j.
 template <int L>
-__device__ __forceinline__ void entry_from_V(const DevSys &S, int e, double t, const double *__restrict__ V,
-                                             const double *__restrict__ HS, double *__restrict__ H,
-                                             double *__restrict__ JH, double *__restrict__ HT = nullptr)
+__device__ __forceinline__ void entry_finish(const DevSys &S, int e, double t, C<L> acc, const double *__restrict__ HS,
+                                             double *__restrict__ H, double *__restrict__ JH, double *__restrict__ HT)
 {
     const int n = S.n;
-    const size_t vplane = (size_t)S.nvar + S.nmon;
     const int i = e / (n + 1), j = e - i * (n + 1);
-    C<L> acc = c_zero<L>();
-    const int r1 = __ldg(S.tptr + e + 1);
-    // unrolled so that the gathers of several contributions are in flight together; the
-    // additions keep their order
-#pragma unroll 4
-    for (int r = __ldg(S.tptr + e); r < r1; r++) acc = c_add(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
     if (t >= 0.0) {
         if (j == n) {
             if (HT) {
@@ -220,6 +212,30 @@ __device__ __forceinline__ void entry_from_V(const DevSys &S, int e, double t, c
         st_c<L>(H, n, i, acc);
     else
         st_c<L>(JH, (size_t)n * n, (size_t)i * n + j, acc);
+}
+
+// The contributions r0 .. r1-1 of the transpose table summed in order
+template <int L>
+__device__ __forceinline__ C<L> sum_contributions(const DevSys &S, int r0, int r1, const double *__restrict__ V)
+{
+    const size_t vplane = (size_t)S.nvar + S.nmon;
+    C<L> acc = c_zero<L>();
+    // unrolled so that the gathers of several contributions are in flight together; the
+    // additions keep their order
+#pragma unroll 4
+    for (int r = r0; r < r1; r++) acc = c_add(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
+    return acc;
+}
+
+// Phase 2 for one entry e: the sum of its contributions in the original monomial order,
+// then the homotopy
+template <int L>
+__device__ __forceinline__ void entry_from_V(const DevSys &S, int e, double t, const double *__restrict__ V,
+                                             const double *__restrict__ HS, double *__restrict__ H,
+                                             double *__restrict__ JH, double *__restrict__ HT = nullptr)
+{
+    const C<L> acc = sum_contributions<L>(S, __ldg(S.tptr + e), __ldg(S.tptr + e + 1), V);
+    entry_finish<L>(S, e, t, acc, HS, H, JH, HT);
 }
 
 // h(z, t) (or f(z) for t < 0) and its Jacobian by the block; entries are taken in the
@@ -320,7 +336,9 @@ __device__ __forceinline__ cdv cdv_fnma(cdv acc, cdv a, cdv b)
 }
 
 // FP64 LU of the leading limbs with partial pivoting (the same pivot rule), block version.
-// B[2][n][n] gets L (unit, below the diagonal), U, and the reciprocals of U's diagonal;
+// B[2][n][n], column-major (entry (i, j) at j n + i, so that the column walks of the
+// pivot search, the multipliers, the trailing update and the triangular solves are
+// contiguous), gets L (unit, below the diagonal), U, and the reciprocals of U's diagonal;
 // PIV[k] is the original row that ends in row k (the row swaps composed).
 template <int L>
 __device__ int block_lu64(int n, const double *__restrict__ A, double *__restrict__ B, int32_t *__restrict__ PIV,
@@ -329,15 +347,16 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
     const int tid = threadIdx.x;
     const size_t ap = (size_t)n * n;
     for (int q = tid; q < n * n; q += HC_TB) {
+        const int j = q / n, i = q - j * n;
         double re, im;
-        ld_lead<L>(A, ap, q, re, im);
+        ld_lead<L>(A, ap, (size_t)i * n + j, re, im);
         B[q] = re;
         B[ap + q] = im;
     }
     for (int q = tid; q < n; q += HC_TB) PIV[q] = q;
     __syncthreads();
-    auto ld = [&](int i, int j) { return cdv{B[(size_t)i * n + j], B[ap + (size_t)i * n + j]}; };
-    auto st = [&](int i, int j, cdv v) { B[(size_t)i * n + j] = v.re; B[ap + (size_t)i * n + j] = v.im; };
+    auto ld = [&](int i, int j) { return cdv{B[(size_t)j * n + i], B[ap + (size_t)j * n + i]}; };
+    auto st = [&](int i, int j, cdv v) { B[(size_t)j * n + i] = v.re; B[ap + (size_t)j * n + i] = v.im; };
     double pmax = 0.0, pmin = INFINITY;
     for (int k = 0; k < n; k++) {
         double bv = -1.0;
@@ -375,7 +394,7 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
         if (tid == 0) st(k, k, inv);
         const int w = n - k - 1;
         for (int idx = tid; idx < w * w; idx += HC_TB) {
-            const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+            const int j = k + 1 + idx / w, i = k + 1 + idx % w;
             st(i, j, cdv_fnma(ld(i, j), ld(i, k), ld(k, j)));
         }
         __syncthreads();
@@ -384,10 +403,10 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
     return HC_OK;
 }
 
-// y = A^-1 r with the FP64 factors of block_lu64, by one warp (the calling warp): r[2][n]
-// in the original row order is permuted into y, then forward and back substitution with
-// warp barriers only.  y must not alias r.  The caller synchronises the block before
-// other warps read y.
+// y = A^-1 r with the (column-major) FP64 factors of block_lu64, by one warp (the calling
+// warp): r[2][n] in the original row order is permuted into y, then forward and back
+// substitution with warp barriers only.  y must not alias r.  The caller synchronises the
+// block before other warps read y.
 __device__ __forceinline__ void warp_lu64_solve(int n, const double *__restrict__ B, const int32_t *__restrict__ PIV,
                                                 const double *__restrict__ r, double *__restrict__ y)
 {
@@ -402,7 +421,7 @@ __device__ __forceinline__ void warp_lu64_solve(int n, const double *__restrict_
     for (int k = 0; k < n - 1; k++) {
         const cdv yk = {y[k], y[n + k]};
         for (int i = k + 1 + lane; i < n; i += 32) {
-            const cdv v = cdv_fnma(cdv{y[i], y[n + i]}, cdv{B[(size_t)i * n + k], B[ap + (size_t)i * n + k]}, yk);
+            const cdv v = cdv_fnma(cdv{y[i], y[n + i]}, cdv{B[(size_t)k * n + i], B[ap + (size_t)k * n + i]}, yk);
             y[i] = v.re;
             y[n + i] = v.im;
         }
@@ -416,7 +435,7 @@ __device__ __forceinline__ void warp_lu64_solve(int n, const double *__restrict_
             y[n + i] = zi.im;
         }
         for (int q = lane; q < i; q += 32) {
-            const cdv v = cdv_fnma(cdv{y[q], y[n + q]}, cdv{B[(size_t)q * n + i], B[ap + (size_t)q * n + i]}, zi);
+            const cdv v = cdv_fnma(cdv{y[q], y[n + q]}, cdv{B[(size_t)i * n + q], B[ap + (size_t)i * n + q]}, zi);
             y[q] = v.re;
             y[n + q] = v.im;
         }
