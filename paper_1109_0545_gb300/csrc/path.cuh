@@ -357,23 +357,31 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
     __syncthreads();
     auto ld = [&](int i, int j) { return cdv{B[(size_t)j * n + i], B[ap + (size_t)j * n + i]}; };
     auto st = [&](int i, int j, cdv v) { B[(size_t)j * n + i] = v.re; B[ap + (size_t)j * n + i] = v.im; };
-    double pmax = 0.0, pmin = INFINITY;
-    for (int k = 0; k < n; k++) {
-        double bv = -1.0;
-        int bi = 0x7fffffff;
-        for (int i = k + tid; i < n; i += HC_TB) {
-            const cdv a = ld(i, k);
-            const double v = add_(mul_(a.re, a.re), mul_(a.im, a.im));
-            if (v > bv) {
-                bv = v;
-                bi = i;
-            }
+    auto mag = [&](cdv a) { return add_(mul_(a.re, a.re), mul_(a.im, a.im)); };
+    // pivot of column 0
+    double bv = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < n; i += HC_TB) {
+        const double v = mag(ld(i, 0));
+        if (v > bv) {
+            bv = v;
+            bi = i;
         }
-        block_argmax(bv, bi, sh);
+    }
+    block_argmax(bv, bi, sh);
+    double pmax = 0.0, pmin = INFINITY;
+    // Two barriers per column: (A) multipliers and row swap, (B) trailing update, which also
+    // finds the next column's pivot (its warps' candidates meet after the barrier)
+    for (int k = 0; k < n; k++) {
         if (!(bv > 0.0)) return HC_SINGULAR;
         pmax = fmax(pmax, bv);
         pmin = fmin(pmin, bv);
         const int piv = bi;
+        // (A) the pivot row's value moves to row k: multipliers of column k from the rows
+        // before the swap (row piv takes the old row k's entry), the other columns swapped
+        const cdv a = ld(piv, k);
+        const cdv inv = {a.re / bv, -a.im / bv};
+        for (int i = k + 1 + tid; i < n; i += HC_TB) st(i, k, cdv_mul(ld(i == piv ? k : i, k), inv));
         if (piv != k) {
             if (tid == 0) {
                 const int t0 = PIV[k];
@@ -381,23 +389,52 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
                 PIV[piv] = t0;
             }
             for (int j = tid; j < n; j += HC_TB) {
+                if (j == k) continue;
                 const cdv t0 = ld(k, j);
                 st(k, j, ld(piv, j));
                 st(piv, j, t0);
             }
         }
         __syncthreads();
-        const cdv a = ld(k, k);
-        const cdv inv = {a.re / bv, -a.im / bv};
-        for (int i = k + 1 + tid; i < n; i += HC_TB) st(i, k, cdv_mul(ld(i, k), inv));
-        __syncthreads();
+        // (B) the reciprocal on the diagonal, the trailing update, the next pivot
         if (tid == 0) st(k, k, inv);
         const int w = n - k - 1;
+        bv = -1.0;
+        bi = 0x7fffffff;
         for (int idx = tid; idx < w * w; idx += HC_TB) {
             const int j = k + 1 + idx / w, i = k + 1 + idx % w;
-            st(i, j, cdv_fnma(ld(i, j), ld(i, k), ld(k, j)));
+            const cdv v = cdv_fnma(ld(i, j), ld(i, k), ld(k, j));
+            st(i, j, v);
+            if (j == k + 1) {
+                const double m = mag(v);
+                if (m > bv || (m == bv && i < bi)) {
+                    bv = m;
+                    bi = i;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (v2 > bv || (v2 == bv && i2 < bi)) {
+                bv = v2;
+                bi = i2;
+            }
+        }
+        if ((tid & 31) == 0) {
+            sh.rv[tid >> 5] = bv;
+            sh.ri[tid >> 5] = bi;
         }
         __syncthreads();
+        bv = sh.rv[0];
+        bi = sh.ri[0];
+#pragma unroll
+        for (int ww = 1; ww < HC_TW; ww++)
+            if (sh.rv[ww] > bv || (sh.rv[ww] == bv && sh.ri[ww] < bi)) {
+                bv = sh.rv[ww];
+                bi = sh.ri[ww];
+            }
     }
     *cond = 0.5 * log10(pmax / pmin);
     return HC_OK;
