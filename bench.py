@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--npts", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--profile-shared", action="store_true",
+                    help="only run the shared-monomial evaluation of Table 1's system (for ncu)")
+    ap.add_argument("--profile-large-path", action="store_true",
+                    help="only run 2 stages of the large QD path on the whole GPU (for ncu)")
     ap.add_argument("--profile-tracker", action="store_true",
                     help="only run a short graph-stepped tracking of 8 uneven paths (for ncu)")
     return ap.parse_args()
@@ -667,10 +671,57 @@ def profile_tracker():
     print(json.dumps({"profile_tracker": [x["n_corr"] for x in st]}))
 
 
+def profile_shared():
+    """Two evaluations with Jacobian of Table 1's common-support system (40 x 40, 200 shared
+    monomials) in DD at 8,192 points, shared-monomial scheme (for profiling)."""
+    import numpy as np
+    import torch
+
+    from paper_1109_0545_gb300 import hc, synth
+    hc.load(build_if_missing=False)
+    s, gamma = synth.common_support_system(1)
+    npts = 8192
+    pts = synth.torus_points(np.random.default_rng(77), npts, s.n)
+    h = hc.system_from(s, 2, gamma)
+    h.set_eval_mode(hc.HC_EVAL_SHARED)
+    x = torch.from_numpy(hc.to_soa(pts, 2)).cuda()
+    f = torch.empty((2, 2, s.npoly, npts), dtype=torch.float64, device="cuda")
+    J = torch.empty((2, 2, s.npoly, s.n, npts), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        hc.hc_eval_jac(h, npts, 0.5, x, f, J)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_shared": npts}))
+
+
+def profile_large_path():
+    """Two corrector stages of the large QD path (n = 96, 98,304 monomials) on the whole GPU
+    (for profiling)."""
+    import numpy as np
+    import torch
+
+    from paper_1109_0545_gb300 import hc, synth
+    hc.load(build_if_missing=False)
+    s, g = synth.large_path_qd(4)
+    h = hc.system_from(s, 4, g)
+    x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 4)])).cuda()
+    x1 = torch.zeros_like(x0)
+    o = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, mode=hc.HC_TRACK_GRID, max_steps=2,
+                                 eps=1e-58, eps_end=1e-58, eps_end_x=1e-58)
+    st = hc.hc_track_path([h], x0, x1, o)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_large_path": int(st[0]["n_corr"])}))
+
+
 def main():
     args = parse()
     if args.profile_tracker:
         profile_tracker()
+        return
+    if args.profile_shared:
+        profile_shared()
+        return
+    if args.profile_large_path:
+        profile_large_path()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -155,9 +155,10 @@ int launch_eval_shared(const DevSys &S, int npts, double t, const double *X, dou
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, false>, 128, 0);
     if (occ < 1) occ = 1;
-    // row groups: enough tasks for about four warps on every SM sub-partition (each group
-    // evaluates every distinct monomial again, so no more groups than that)
-    const long long want = (long long)sms * 4 * 4;
+    // row groups: the fewest that give two warps' tasks on every SM sub-partition (each group
+    // evaluates every distinct monomial again; at 8,192 points 10 groups ran 2,560 tasks on
+    // 2,432 resident warps, a second round for 128 of them)
+    const long long want = (long long)sms * 4 * 2;
     long long groups = (want + ntiles - 1) / ntiles;
     if (groups < 1) groups = 1;
     if (groups > S.npoly) groups = S.npoly;
