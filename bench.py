@@ -152,8 +152,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot_t / max(len(steps), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "npts": args.npts, "n": 32, "precision": "complex DD",
-                   "lu": "FP64 LU + DD refinement"},
+        "config": {"workload": WORKLOAD, "npts": args.npts, "n": s.n, "monomials": s.nmon,
+                   "precision": "complex double-double", "lu": "FP64 LU + DD refinement",
+                   "max_refine": MAX_REFINE, "t": T_HOM, "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
                          "sample": f"{steps[0][0] if steps else 0} points per step "
                                    f"(about {budget:.0f} s of oracle work), all host cores"},
