@@ -27,6 +27,11 @@
  *   - one Newton step (Alg. 4.1), native or FP64 LU with L-limb refinement;
  *   - the path tracker loop of Alg. 3.1 with a secant or quadratic (Sec. 5) predictor.
  *
+ * Pins (tests/test_oracle_pins.py) tie each routine to exact rationals, sympy, mpmath or
+ * closed forms.  Parity unpinned: the exact stage-by-stage trajectory of or_track for
+ * n > 1.  Only its invariants (steps on the lambda0 2^-j lattice, accepted steps adding up
+ * to 1), its univariate end points and the start-system roots are pinned.
+ *
  * Readings of the paper where it is silent or garbled are stated at each routine.
  * Layout of every array here is point-major, array-of-structures:
  *   x[p][j][2][L], f[p][i][2][L], J[p][i][j][2][L], coef[m][2][L] (re limbs, im limbs).
