@@ -273,6 +273,18 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
                           "same_end_point_as_batched_all_dd_1e-28": same,
                           "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
         out[name] = res
+    # the full uneven-path workload: 8,192 systems, 200 stages each, batched secant tracker
+    fam = [synth.uneven_path_system(3, j) for j in range(8192)]
+    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+    st, _, dt = run(systems, gammas, hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, max_steps=cap))
+    steps = sum(x["n_corr"] for x in st)
+    gops = sum((x["newton_its"] + x["end_its"]) * opcount.newton_iteration_ops(sy, 2)
+               for x, sy in zip(st, systems)) / dt / 1e9
+    out["uneven_8192_paths"] = {"paths": 8192, "stage_cap": cap, "path_steps_per_s": steps / dt,
+                                "seconds": dt, "fp64_gops_at_least": gops,
+                                "fp64_frac_of_measured_peak_at_least": gops / peak_gops if peak_gops else None,
+                                "speedup_steps_vs_plain":
+                                    (steps / dt) / out["uneven"]["plain_one_path_per_launch"]["path_steps_per_s"]}
     return out
 
 
@@ -444,6 +456,49 @@ def quality_up_bench(torch, hc, synth, npaths=456):
     return out
 
 
+def mlp_bench(torch, hc, steps=200, batch=8192, nrec=65536):
+    """The step proposer's kernels: one training step (k_mlp_grad + k_mlp_reduce +
+    k_mlp_adamw on a batch of 8,192 feature records, the batch of the proposer's training)
+    and inference (k_mlp_forward) on 65,536 records, on seeded synthetic records of the
+    logged shapes.  Times from CUDA events on the launching stream."""
+    import numpy as np
+    from paper_1109_0545_gb300 import learn
+    rng = np.random.default_rng(55)
+    X = torch.from_numpy(rng.normal(0.0, 0.5, (nrec, hc.HC_MLP_IN)).astype(np.float32)).cuda()
+    r = torch.from_numpy(rng.uniform(-1.5, 1.5, nrec).astype(np.float32)).cuda()
+    a = torch.from_numpy((rng.uniform(size=nrec) < 0.75).astype(np.int32)).cuda()
+    p = torch.from_numpy(learn.init_params(0)).cuda()
+    m1, m2, g = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    out = torch.empty(nrec, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def train_step(k):
+        hc.hc_mlp_grad(p, batch, X, r, a, learn.KAPPA, g, loss, stream)
+        hc.hc_mlp_adamw(p, m1, m2, g, k, 1e-3, 0.9, 0.999, 1e-8, 1e-4, stream)
+
+    for k in range(1, 6):
+        train_step(k)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(6, 6 + steps):
+        train_step(k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_train = ev0.elapsed_time(ev1) / steps
+    hc.hc_mlp_forward(p, nrec, X, out, stream)
+    ev0.record(stream)
+    for _ in range(10):
+        hc.hc_mlp_forward(p, nrec, X, out, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = ev0.elapsed_time(ev1) / 10
+    return {"train_step_ms": ms_train, "train_records_per_s": batch / (ms_train * 1e-3),
+            "batch": batch, "forward_ms_65536_records": ms_fwd,
+            "forward_records_per_s": nrec / (ms_fwd * 1e-3)}
+
+
 def rank_points(rank: int, npts: int, n: int, default):
     """The points rank `rank` evaluates: rank 0 the workload's own, every other rank its
     own seeded draw of the same size (independent problems: weak scaling)."""
@@ -591,17 +646,33 @@ def run_gpu(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         ms_qd = ev0.elapsed_time(ev1)
-        sysq.free()
-        del xq, fq, Jq
+        del fq, Jq
+        # refinement sweeps per accuracy level: one Newton step (FP64 LU + refinement) at
+        # the same 16,384 points in complex double and QD (DD: the timed step above)
+        sweeps_by_prec = {}
+        for Lq, hq in ((1, hc.system_from(s, 1, gamma)), (4, sysq)):
+            xl = torch.from_numpy(hc.to_soa(pts[:q], Lq)).cuda()
+            rl = torch.zeros(q, dtype=torch.float64, device="cuda")
+            sl = torch.zeros(q, dtype=torch.int32, device="cuda")
+            wl = torch.zeros(q, dtype=torch.int32, device="cuda")
+            hc.hc_newton_step(hq, q, T_HOM, xl, hc.HC_LU_FP64_REFINE, MAX_REFINE, rl, sl, wl, stream)
+            torch.cuda.synchronize()
+            sweeps_by_prec[{1: "double", 4: "quad_double"}[Lq]] = np.bincount(
+                wl.cpu().numpy(), minlength=MAX_REFINE + 1).tolist()
+            hq.free()
+            del xl, rl, sl, wl
+        del xq
         extras = {"tracker": tracker_bench(torch, hc, synth, peak_gops),
                   "paper_tables": paper_tables_bench(torch, hc, synth),
                   "common_support_table1": common_support_bench(torch, hc, synth, peak_gops),
                   "quality_up": quality_up_bench(torch, hc, synth),
+                  "proposer_mlp": mlp_bench(torch, hc),
                   "eval_jac_qd_points_per_s": q / (ms_qd * 1e-3),
                   "eval_jac_qd_fp64_gops": opcount.eval_ops_per_point(s, 4) * q / (ms_qd * 1e-3) / 1e9,
                   "newton_native_dd_lu_points_per_s": npts / (ms_native * 1e-3),
                   "eval_jac_points_per_s": npts / (ms_eval * 1e-3),
                   "refine_sweeps_hist": np.bincount(sweeps, minlength=MAX_REFINE + 1).tolist(),
+                  "refine_sweeps_hist_16384pts": sweeps_by_prec,
                   "status_ok_frac": float(np.mean(status == hc.HC_OK))}
 
     # end to end through the public API with host buffers (pinned), copies timed

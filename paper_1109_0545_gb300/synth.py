@@ -12,8 +12,10 @@ Recipe (the paper's own generator is not specified, Sec. 4, 5 and 7 describe onl
     double, lower limbs zero;
   * points are uniform on the unit torus |x_j| = 1;
   * gamma is exp(i theta) for one more uniform theta.
-Draw order for one system: for each polynomial, for each monomial: k (if ranged), the
-support, the exponents, theta; then a constant-term theta if requested.  numpy's
+Draw order for one random system (vectorised over the whole system): the monomial count
+of every polynomial (if ranged), the k of every monomial (if ranged), one uniform key per
+(monomial, variable) (the support is the k variables with the smallest keys, sorted), the
+exponents, the coefficient angles, then the constant-term angles if requested.  numpy's
 default_rng(seed) generates everything; a family of systems uses default_rng([seed, j])
 for system j, so system j can be drawn without the others.
 """
@@ -70,36 +72,44 @@ def _draw(rng, v):
 def random_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
                   const_term: bool = False, npoly: int | None = None) -> System:
     """One random system.  mons_per_poly and k are ints or inclusive (lo, hi) ranges,
-    exps is an inclusive (lo, hi) range."""
+    exps is an inclusive (lo, hi) range.  Drawn whole-system at a time (vectorised): the
+    monomial counts of all polynomials, the k of every monomial, one uniform key per
+    (monomial, variable) whose k smallest give the support (a uniform k-subset), the
+    exponents, the coefficient angles, then the constant terms' angles."""
     npoly = n if npoly is None else npoly
-    mon_ptr = [0]
-    var_ptr = [0]
-    idx: list[np.ndarray] = []
-    ex: list[np.ndarray] = []
-    thetas: list[float] = []
-    for _ in range(npoly):
-        m_i = _draw(rng, mons_per_poly)
-        for _ in range(m_i):
-            kk = _draw(rng, k)
-            sup = np.sort(rng.choice(n, size=kk, replace=False)).astype(np.int32)
-            e = rng.integers(exps[0], exps[1] + 1, size=kk).astype(np.int32)
-            idx.append(sup)
-            ex.append(e)
-            var_ptr.append(var_ptr[-1] + kk)
-            thetas.append(rng.uniform(0.0, 2.0 * np.pi))
-        cnt = m_i
-        if const_term:
-            var_ptr.append(var_ptr[-1])
-            thetas.append(rng.uniform(0.0, 2.0 * np.pi))
-            cnt += 1
-        mon_ptr.append(mon_ptr[-1] + cnt)
-    th = np.array(thetas)
-    return System(n=n, npoly=npoly,
-                  mon_ptr=np.array(mon_ptr, dtype=np.int32),
-                  var_ptr=np.array(var_ptr, dtype=np.int32),
-                  var_idx=np.concatenate(idx).astype(np.int32) if idx else np.zeros(0, np.int32),
-                  var_exp=np.concatenate(ex).astype(np.int32) if ex else np.zeros(0, np.int32),
-                  coef=np.cos(th) + 1j * np.sin(th))
+    if isinstance(mons_per_poly, tuple):
+        m = rng.integers(mons_per_poly[0], mons_per_poly[1] + 1, size=npoly)
+    else:
+        m = np.full(npoly, int(mons_per_poly))
+    mt = int(m.sum())
+    if isinstance(k, tuple):
+        ks = rng.integers(k[0], k[1] + 1, size=mt)
+    else:
+        ks = np.full(mt, int(k))
+    keys = rng.random((mt, n))
+    order = np.argsort(keys, axis=1)
+    kmax = int(ks.max()) if mt else 0
+    sup = np.sort(np.where(np.arange(kmax)[None, :] < ks[:, None], order[:, :kmax], n), axis=1)
+    var_idx = sup[sup < n].astype(np.int32)      # row by row, each row sorted
+    var_exp = rng.integers(exps[0], exps[1] + 1, size=int(ks.sum())).astype(np.int32)
+    th = rng.uniform(0.0, 2.0 * np.pi, size=mt)
+    coef = np.cos(th) + 1j * np.sin(th)
+    var_ptr = np.concatenate([[0], np.cumsum(ks)])
+    if not const_term:
+        mon_ptr = np.concatenate([[0], np.cumsum(m)])
+        return System(n=n, npoly=npoly, mon_ptr=mon_ptr.astype(np.int32), var_ptr=var_ptr.astype(np.int32),
+                      var_idx=var_idx, var_exp=var_exp, coef=coef)
+    # a constant term (k = 0) closes every polynomial
+    thc = rng.uniform(0.0, 2.0 * np.pi, size=npoly)
+    ends = np.cumsum(m)
+    pos = ends + np.arange(1, npoly + 1) - 1           # index of polynomial i's constant
+    mon_ptr = np.concatenate([[0], ends + np.arange(1, npoly + 1)])
+    kk = np.insert(ks, ends, 0)
+    allc = np.insert(coef, ends, np.cos(thc) + 1j * np.sin(thc))
+    assert np.all(kk[pos] == 0)
+    return System(n=n, npoly=npoly, mon_ptr=mon_ptr.astype(np.int32),
+                  var_ptr=np.concatenate([[0], np.cumsum(kk)]).astype(np.int32),
+                  var_idx=var_idx, var_exp=var_exp, coef=allc)
 
 
 def torus_points(rng: np.random.Generator, npts: int, n: int) -> np.ndarray:
@@ -154,28 +164,17 @@ def fixed_degree_system(rng: np.random.Generator, n: int, mons_per_poly, degree:
 def _with_leading_powers(s: System, lead: int) -> System:
     """s plus, in polynomial i, the monomial x_i^D with coefficient 1, D = max(lead, 1 + the
     largest total degree in s), placed last in the polynomial."""
-    top = 0
-    for m in range(s.nmon):
-        top = max(top, int(s.var_exp[s.var_ptr[m]:s.var_ptr[m + 1]].sum()))
+    cs = np.concatenate([[0], np.cumsum(s.var_exp, dtype=np.int64)])
+    top = int((cs[s.var_ptr[1:]] - cs[s.var_ptr[:-1]]).max()) if s.nmon else 0
     lead = max(lead, top + 1)
-    mon_ptr = [0]
-    var_ptr = [0]
-    idx, ex, coef = [], [], []
-    for i in range(s.npoly):
-        for m in range(s.mon_ptr[i], s.mon_ptr[i + 1]):
-            q0, q1 = s.var_ptr[m], s.var_ptr[m + 1]
-            idx.extend(s.var_idx[q0:q1])
-            ex.extend(s.var_exp[q0:q1])
-            var_ptr.append(var_ptr[-1] + (q1 - q0))
-            coef.append(s.coef[m])
-        idx.append(i)
-        ex.append(lead)
-        var_ptr.append(var_ptr[-1] + 1)
-        coef.append(1.0 + 0j)
-        mon_ptr.append(len(coef))
-    return System(n=s.n, npoly=s.npoly, mon_ptr=np.array(mon_ptr, np.int32),
-                  var_ptr=np.array(var_ptr, np.int32), var_idx=np.array(idx, np.int32),
-                  var_exp=np.array(ex, np.int32), coef=np.array(coef))
+    ends = s.mon_ptr[1:]                      # the new monomial goes after these
+    ks = np.insert(np.diff(s.var_ptr), ends, 1)
+    vpos = s.var_ptr[ends]
+    return System(n=s.n, npoly=s.npoly, mon_ptr=(s.mon_ptr + np.arange(s.npoly + 1)).astype(np.int32),
+                  var_ptr=np.concatenate([[0], np.cumsum(ks)]).astype(np.int32),
+                  var_idx=np.insert(s.var_idx, vpos, np.arange(s.npoly)).astype(np.int32),
+                  var_exp=np.insert(s.var_exp, vpos, lead).astype(np.int32),
+                  coef=np.insert(s.coef, ends, 1.0 + 0j))
 
 
 def regular_system(rng: np.random.Generator, n: int, mons_per_poly, k, exps,
