@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--npts", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--full-uneven", action="store_true",
+                    help="also track all 8,192 systems of the uneven-path family (about a minute more)")
     ap.add_argument("--profile-shared", action="store_true",
                     help="only run the shared-monomial evaluation of Table 1's system (for ncu)")
     ap.add_argument("--profile-large-path", action="store_true",
@@ -190,7 +192,8 @@ def captured_traffic(npts: int):
 PROPOSER = os.path.join(ROOT, "paper_1109_0545_gb300", "data", "proposer_weights.npy")
 
 
-def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=2432, cap=200, plain_sample=2):
+def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=2432, cap=200, plain_sample=2,
+                  full_uneven=False):
     """Path steps/s and paths/s of the batched tracker (all paths in one persistent
     kernel, FP64 LU + DD refinement; secant, quadratic, tangent, and quadratic + learned step
     proposer) against the plain GPU tracker (all-DD elimination, secant, plain step
@@ -199,7 +202,8 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
     systems, four waves of four blocks on each of 152 SMs), whose paths all diverge,
     tracked for at most `cap` stages each (path steps/s); and its regular variant (a pure
     power and a constant per polynomial, seed 33; npaths = 608, one wave), tracked to the
-    end (paths/s, end points compared with the batched all-DD tracker's at 1e-28).  FP64 throughput: the
+    end (paths/s, end points compared with the batched all-DD tracker's at 1e-28); with
+    full_uneven, also all 8,192 systems of the uneven family, 200 stages each.  FP64 throughput: the
     Newton iterations of all paths (end game included) times the FP64 instructions of one
     iteration without its refinement sweeps (`opcount.newton_iteration_ops`, a lower bound)
     per second, against the measured FP64 peak."""
@@ -209,8 +213,8 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
     if os.path.exists(PROPOSER):
         prop = torch.from_numpy(np.load(PROPOSER).astype(np.float32)).cuda()
 
-    def run(systems, gammas, opts):
-        handles = [hc.system_from(s, 2, g) for s, g in zip(systems, gammas)]
+    def run(handles, systems, opts):
+        """One tracking call on already loaded systems (loading is outside the timing)."""
         x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 2) for s in systems])).cuda()
         x1 = torch.zeros_like(x0)
         torch.cuda.synchronize()
@@ -218,8 +222,6 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
         stats = hc.hc_track_path(handles, x0, x1, opts)
         dt = time.perf_counter() - t0
         ends = hc.unpack_paths(x1.cpu().numpy(), [s.n for s in systems], 2)
-        for h in handles:
-            h.free()
         return stats, ends, dt
 
     rng = np.random.default_rng(33)
@@ -240,15 +242,16 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
     out = {}
     for name, (fam, extra) in fams.items():
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
+        handles = [hc.system_from(sy, 2, g) for sy, g in fam]
         npaths = len(systems)
         it_ops = [opcount.newton_iteration_ops(sy, 2) for sy in systems]
         plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE, **extra)
         p_steps, p_dt = 0, 0.0
         for j in range(plain_sample):
-            pst, _, pdt = run(systems[j:j + 1], gammas[j:j + 1], plain)
+            pst, _, pdt = run(handles[j:j + 1], systems[j:j + 1], plain)
             p_steps += pst[0]["n_corr"]
             p_dt += pdt
-        ref_st, ref_ends, ref_dt = run(systems, gammas, plain)
+        ref_st, ref_ends, ref_dt = run(handles, systems, plain)
         ref_steps = sum(x["n_corr"] for x in ref_st)
         res = {"paths": npaths, "stage_cap": extra.get("max_steps"),
                "plain_one_path_per_launch": {"path_steps_per_s": p_steps / p_dt,
@@ -257,7 +260,7 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
                "batched_all_dd_secant": {"path_steps_per_s": ref_steps / ref_dt,
                                          "paths_per_s": npaths / ref_dt}}
         for vname, kw in variants:
-            st, ends, dt = run(systems, gammas, hc.hc_track_opts_default(**kw, **extra))
+            st, ends, dt = run(handles, systems, hc.hc_track_opts_default(**kw, **extra))
             steps = sum(x["n_corr"] for x in st)
             same = sum(1 for p in range(npaths) if st[p]["status"] == hc.HC_OK and ref_st[p]["status"] == hc.HC_OK
                        and np.abs((ends[p] - ref_ends[p]).sum(-1)).max()
@@ -272,11 +275,18 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
                           "ok_paths": sum(1 for x in st if x["status"] == hc.HC_OK),
                           "same_end_point_as_batched_all_dd_1e-28": same,
                           "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
+        for h in handles:
+            h.free()
         out[name] = res
+    if not full_uneven:
+        return out
     # the full uneven-path workload: 8,192 systems, 200 stages each, batched secant tracker
     fam = [synth.uneven_path_system(3, j) for j in range(8192)]
-    systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
-    st, _, dt = run(systems, gammas, hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, max_steps=cap))
+    systems = [f[0] for f in fam]
+    handles = [hc.system_from(sy, 2, g) for sy, g in fam]
+    st, _, dt = run(handles, systems, hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, max_steps=cap))
+    for h in handles:
+        h.free()
     steps = sum(x["n_corr"] for x in st)
     gops = sum((x["newton_its"] + x["end_its"]) * opcount.newton_iteration_ops(sy, 2)
                for x, sy in zip(st, systems)) / dt / 1e9
@@ -662,7 +672,7 @@ def run_gpu(args):
             hq.free()
             del xl, rl, sl, wl
         del xq
-        extras = {"tracker": tracker_bench(torch, hc, synth, peak_gops),
+        extras = {"tracker": tracker_bench(torch, hc, synth, peak_gops, full_uneven=args.full_uneven),
                   "paper_tables": paper_tables_bench(torch, hc, synth),
                   "common_support_table1": common_support_bench(torch, hc, synth, peak_gops),
                   "quality_up": quality_up_bench(torch, hc, synth),
