@@ -104,6 +104,24 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.hc_eval_jac(None, 1, 0.5, None, None, None, None) == hc.HC_EINVAL
     assert lib.hc_newton_step(None, 1, 0.5, None, 0, 1, None, None, None, None) == hc.HC_EINVAL
     lib.hc_system_free(None)  # no-op
+    assert lib.hc_system_set_eval_mode(None, hc.HC_EVAL_SHARED) == hc.HC_EINVAL
+    assert lib.hc_system_eval_mode(None, None, None) == hc.HC_EINVAL
+    assert lib.hc_system_info(None, None, None, None, None, None, None, None) == hc.HC_EINVAL
+    # the tracker validates its arguments (and options) before touching the device
+    opts = hc.hc_track_opts_default()
+    stats = (hc.PathStats * 1)()
+    assert lib.hc_track_path(None, 1, None, None, ct.byref(opts), stats, None, 0, None) == hc.HC_EINVAL
+    assert lib.hc_last_error()  # a message says why
+
+
+def test_option_defaults_follow_the_readings():
+    """The defaults of hc_track_opts_default are the readings of Alg. 3.1's constants:
+    lambda0 0.01, halve on failure, double after 3 successes up to 0.08 (the 0.01 2^j
+    lattice of Tables 2-3), lambda_min 1e-12, 3 Newton iterations per stage."""
+    o = hc.hc_track_opts_default()
+    assert (o.lambda0, o.shrink, o.grow, o.grow_after, o.lambda_max) == (0.01, 0.5, 2.0, 3, 0.08)
+    assert (o.lambda_min, o.max_it, o.max_steps) == (1e-12, 3, 100000)
+    assert o.predictor == hc.HC_PRED_SECANT and o.explore == 0.0 and not o.proposer
 
 
 def test_layout_round_trip():
