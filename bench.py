@@ -519,6 +519,25 @@ def rank_points(rank: int, npts: int, n: int, default):
     return synth.torus_points(np.random.default_rng([2, rank]), npts, n)
 
 
+def shard_range(nunits: int, rank: int, world: int) -> tuple[int, int]:
+    """The block of independent units (paths, points) rank `rank` of `world` takes: the
+    first nunits % world ranks take one more; no unit is shared, so the ranks need no
+    exchange until the results are gathered."""
+    base, extra = divmod(nunits, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def gather_stats(stats: list, dist) -> list:
+    """The per-unit results of every rank, in rank order, on every rank (the one gather of
+    a sharded run)."""
+    if dist is None:
+        return list(stats)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, list(stats))
+    return [x for part in parts for x in part]
+
+
 def max_over_ranks(ms: float, dist, device=None) -> float:
     """The slowest rank's time (the job's time); the only collective of the bench."""
     if dist is None:
@@ -624,7 +643,9 @@ def run_gpu(args):
                 "traffic_note": "ncu dram read+write per launch, 8,192-point capture scaled by points"}
 
     extras = {}
-    if not args.no_extras:
+    # the secondary measurements are single-GPU figures: with several ranks they would hold
+    # every GPU for minutes, so they run at N = 1 only
+    if not args.no_extras and world == 1:
         # the plain all-DD elimination, and evaluation alone, same points
         def timed(fn, reps=3):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -1,6 +1,7 @@
 """The multi-rank path of bench.py on CPU: two gloo ranks, each with its own points,
 combine nothing but the slowest time (the only collective), and the whole-job value is
-the units of all ranks over that time."""
+the units of all ranks over that time; paths shard in blocks and their results gather
+once, in order."""
 import os
 import socket
 
@@ -49,3 +50,34 @@ def test_two_gloo_ranks_share_only_the_max_time():
     npts, steps = 64, 3
     value = npts * world * steps / (res[0][2] * steps * 1e-3)
     assert value == pytest.approx(npts * world / 0.150)
+
+
+def _path_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    lo, hi = bench.shard_range(9, rank, world)
+    # each rank "tracks" its own block of paths (here: records the path index it owns)
+    mine = [{"path": p, "rank": rank} for p in range(lo, hi)]
+    out[rank] = bench.gather_stats(mine, dist)
+    dist.destroy_process_group()
+
+
+def test_paths_shard_in_blocks_and_gather_in_order():
+    import bench
+    for n in (0, 1, 7, 9, 8192):
+        for world in (1, 2, 3, 8):
+            blocks = [bench.shard_range(n, r, world) for r in range(world)]
+            assert blocks[0][0] == 0 and blocks[-1][1] == n
+            assert all(blocks[r][1] == blocks[r + 1][0] for r in range(world - 1))
+            sizes = [b - a for a, b in blocks]
+            assert max(sizes) - min(sizes) <= 1
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_path_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        assert [x["path"] for x in res[r]] == list(range(9))
+        assert [x["rank"] for x in res[r]] == [0] * 5 + [1] * 4
