@@ -93,7 +93,8 @@ int hc_system_info(const hc_system *sys, int *n, int *npoly, int *nmon, int *nva
 
 /*
  * hc_eval_jac -- values and full Jacobian at npts points (Alg. 4.1 Monomial_Evaluation
- * followed by Coefficient_Product; the monomial scheme of Sec. 6).
+ * followed by Coefficient_Product; the monomial scheme of Sec. 6), per term or with
+ * shared monomials (hc_system_set_eval_mode; the same values up to rounding).
  *   t < 0   evaluate f itself (npoly may differ from n);
  *   t >= 0  evaluate the homotopy h(., t) and its Jacobian in x (requires npoly == n
  *           and every d_i >= 1).
@@ -126,8 +127,8 @@ int hc_newton_step(hc_system *sys, int npts, double t, double *x, int lu_mode,
                    void *stream);
 
 /*
- * hc_set_tiles -- tile shape of the evaluation kernels for every later call in this
- * process (the autotuner's knob; 0 = automatic):
+ * hc_set_tiles -- tile shape of the per-term evaluation kernel for every later call in
+ * this process (the autotuner's knob; 0 = automatic):
  *   rows_per_task  polynomials one warp evaluates per task (its 32 points each)
  *   blocks_per_sm  resident 4-warp blocks per SM of the persistent grid (<= 32)
  * Process-wide host-side setting, not synchronised with calls in other threads; any
@@ -250,8 +251,10 @@ void hc_track_opts_default(hc_track_opts *opts);
  *   stats  host, npaths results, valid on return
  *   log    device, npaths * log_cap records (record s of path p at p * log_cap + s),
  *          or NULL with log_cap = 0
- * One thread block per path (HC_TRACK_GRID: the whole GPU per path, paths in turn).
- * Synchronises the stream before returning.  Allocates and
+ * One thread block per path (HC_TRACK_GRID: the whole GPU per path, paths in turn);
+ * blocks take paths largest first (by the cost of a stage), the first wave in a fixed
+ * shuffled order.  Each path's result does not depend on the order, the mode or the
+ * other paths (bit for bit).  Synchronises the stream before returning.  Allocates and
  * frees its own workspace.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA, HC_ETIMEOUT (graph
  * mode only: paths still unfinished after max_steps / graph_steps + 2 replays).
  */
