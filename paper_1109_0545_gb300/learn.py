@@ -167,9 +167,19 @@ def main():
     ap.add_argument("--margins", default="0.5")
     ap.add_argument("--explore", type=float, default=1.5,
                     help="log2 range of the random step perturbation while collecting")
+    ap.add_argument("--eval-only", default=None,
+                    help="skip collection and training: evaluate these saved weights")
     args = ap.parse_args()
     import torch
     hc.load(build_if_missing=False)
+    if args.eval_only:
+        params = torch.from_numpy(np.load(args.eval_only).astype(np.float32)).cuda()
+        res = {"weights": os.path.basename(args.eval_only)}
+        res.update(evaluate_families(torch, params, args))
+        with open(args.out, "w") as fh:
+            json.dump(res, fh, indent=1)
+        print(json.dumps(res))
+        return
     # the plain controller with its steps perturbed by 2^u, u uniform in
     # [-explore, explore], so that the logs hold accepted and rejected steps over a range
     # of ratios around the plain choice
@@ -212,9 +222,21 @@ def main():
            "collect_s": t_collect,
            "train_s": t_train, "train_steps": args.steps, "loss_first": losses[0],
            "loss_last": losses[-1]}
+    res.update(evaluate_families(torch, params, args))
+    with open(args.out, "w") as fh:
+        json.dump(res, fh, indent=1)
+    print(json.dumps(res))
+
+
+def evaluate_families(torch, params, args) -> dict:
+    """The proposer against the plain controller on held-out seed-20 paths: the uneven
+    family and its regular variant, at each margin."""
+    res = {}
     margins = [float(v) for v in args.margins.split(",")]
     for fam_name, fam in (("uneven_seed20", [synth.uneven_path_system(20, k) for k in range(args.uneven_eval_paths)]),
                           ("uneven_regular_seed20", regular_family(20, args.eval_paths))):
+        if not fam:
+            continue
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
         res[fam_name] = {}
         for margin in margins:
@@ -232,9 +254,7 @@ def main():
             r["status_plain"] = np.bincount([x["status"] for x in ev["plain"]["stats"]], minlength=7).tolist()
             r["status_proposer"] = np.bincount([x["status"] for x in ev["proposer"]["stats"]], minlength=7).tolist()
             res[fam_name][f"margin_{margin}"] = r
-    with open(args.out, "w") as fh:
-        json.dump(res, fh, indent=1)
-    print(json.dumps(res))
+    return res
 
 
 if __name__ == "__main__":
