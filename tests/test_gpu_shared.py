@@ -77,3 +77,34 @@ def test_scheme_choice_at_load():
     h2 = hc.system_from(s2, 2, g2)
     assert h2.eval_mode()[0] == hc.HC_EVAL_PER_TERM
     h2.free()
+
+
+def test_shared_scheme_edge_cases():
+    """A monomial repeated inside one polynomial and across polynomials, a polynomial that is
+    only a constant, k = 1 and k = 32 monomials, exponent 64, a ragged tile, and npts = 0."""
+    torch = torch_cuda()
+    n = 32
+    # poly 0: x0^3 x5, x0^3 x5 again, constant; poly 1: constant only;
+    # poly 2: all 32 variables, x0^3 x5 (shared with poly 0), x31^64
+    idx = [0, 5, 0, 5] + list(range(32)) + [0, 5, 31]
+    ex = [3, 1, 3, 1] + [1] * 16 + [2] * 16 + [3, 1, 64]
+    var_ptr = [0, 2, 4, 4, 4, 36, 38, 39]
+    s = synth.System(n=n, npoly=3, mon_ptr=np.array([0, 3, 4, 7], np.int32),
+                     var_ptr=np.array(var_ptr, np.int32), var_idx=np.array(idx, np.int32),
+                     var_exp=np.array(ex, np.int32), coef=np.exp(1j * np.arange(7.0)))
+    rng = np.random.default_rng(530)
+    gamma = synth.unit_complex(rng)
+    for L in (2, 4):
+        pts = limbs_of(synth.torus_points(rng, 37, n), L)
+        fo, Jo = oracle_eval(s, gamma, L, pts, -1.0)
+        f, J = gpu_eval(torch, s, gamma, L, pts, -1.0, mode=hc.HC_EVAL_SHARED)
+        assert np.all(rel_err_per_point(f, fo) <= TOL[L])
+        assert np.all(rel_err_per_point(J, Jo) <= TOL[L])
+    h = hc.system_from(s, 2, gamma)
+    h.set_eval_mode(hc.HC_EVAL_SHARED)
+    x = torch.zeros((2, 2, n, 1), dtype=torch.float64, device="cuda")
+    f = torch.full((2, 2, 3, 1), 7.0, dtype=torch.float64, device="cuda")
+    hc.hc_eval_jac(h, 0, -1.0, x, f, None)    # npts = 0: nothing is written
+    torch.cuda.synchronize()
+    assert torch.all(f == 7.0)
+    h.free()
