@@ -406,9 +406,9 @@ def quality_up_bench(torch, hc, synth, npaths=456):
     tolerances 1e-12 / 1e-26 / 1e-58).  Quality Q = correct decimal places of the end
     points (median over converged paths; the QD end points are the reference for double
     and DD, the DD ones bound QD from below at its own tolerance).  The paper's quality up
-    at fixed time, y(p) = 1 + (Q_QD/Q_DD - 1)(p - 1)/(p* - 1), with p* = T_QD/T_DD the GPUs
-    that QD needs to match the time of DD on one GPU (perfect weak scaling assumed, as the
-    paper assumes optimal speedup), is reported for p = 8 GPUs."""
+    at fixed time (`quality.py`, Sec. 2): p* = ceil(T_QD / T_DD) GPUs let QD match the time
+    of DD on one GPU (optimal speedup assumed, as in the paper), and y(p) runs linearly from
+    y(1) = 1 to y(p*) = Q_QD / Q_DD; reported for p = 8 GPUs."""
     import numpy as np
     rng = np.random.default_rng(44)
     fam = []
@@ -456,13 +456,16 @@ def quality_up_bench(torch, hc, synth, npaths=456):
     out["double"]["digits_vs_qd"] = digits(1)
     out["double_double"]["digits_vs_qd"] = digits(2)
     # QD's own quality: its corrector tolerance (the end game stops at 1e-58 relative)
+    from paper_1109_0545_gb300 import quality
     q_dd = out["double_double"]["digits_vs_qd"]
     q_qd = 58.0
-    p_star = out["quad_double"]["seconds"] / out["double_double"]["seconds"]
     out["quad_double"]["digits"] = q_qd
-    out["qd_time_over_dd_time"] = p_star
-    if q_dd and p_star > 1.0:
-        out["quality_up_8_gpus"] = 1.0 + (q_qd / q_dd - 1.0) * (8 - 1) / (p_star - 1.0) if p_star > 8 else q_qd / q_dd
+    ratio, p_star = quality.processors_for_fixed_time(out["double_double"]["seconds"],
+                                                      out["quad_double"]["seconds"], 1)
+    out["qd_time_over_dd_time"] = ratio
+    out["qd_gpus_for_dd_time"] = p_star
+    if q_dd:
+        out["quality_up_8_gpus"] = quality.quality_up(8, p_star, q_qd / q_dd)
     return out
 
 
