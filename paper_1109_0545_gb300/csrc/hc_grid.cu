@@ -232,14 +232,22 @@ template <int L> __global__ void __launch_bounds__(32) k_g_refine_rows(GArgs a)
     }
 }
 
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_refine_solve(GArgs a)
+template <int L> __global__ void __launch_bounds__(HC_TB) k_g_refine_solve(GArgs a, int b_smem)
 {
     __shared__ BlockShared sh;
-    extern __shared__ double ysh[];  // [2][n]
+    extern __shared__ double ysh[];  // [2][n], then (b_smem) a copy of the factors [2][n][n]
     GStage &g = *a.g;
     if (!g_active(g) || !g.refine_active) return;
     const int n = a.S.n, tid = threadIdx.x;
-    if (tid < 32) warp_lu64_solve(n, a.B, a.PIV, a.RV, ysh);
+    // the solve's column walks are dependent loads: from shared memory, not L2
+    const double *Bf = a.B;
+    if (b_smem) {
+        double *Bs = ysh + 2 * n;
+        for (int q = tid; q < 2 * n * n; q += HC_TB) Bs[q] = a.B[q];
+        __syncthreads();
+        Bf = Bs;
+    }
+    if (tid < 32) warp_lu64_solve(n, Bf, a.PIV, a.RV, ysh);
     __syncthreads();
     double dn = 0.0, zz = 0.0;
     for (int i = tid; i < n; i += HC_TB) {
@@ -326,12 +334,14 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
     const int mblocks = (a.S.nmon + HC_TB - 1) / HC_TB;
     const int eblocks = (a.S.npoly * (a.S.n + 1) + HC_TB - 1) / HC_TB;
     const size_t ysh_bytes = sizeof(double) * 2 * (size_t)a.S.n;  // n <= 256: at most 4 KiB
-    // the FP64 LU in shared memory when the factors fit (n <= 110)
+    // the FP64 LU and the refinement solves in shared memory when the factors fit (n <= 110)
     const size_t bsm = sizeof(double) * 2 * (size_t)a.S.n * a.S.n;
     const int b_smem = ysh_bytes + bsm <= 200 * 1024;
     const size_t fac_bytes = ysh_bytes + (b_smem ? bsm : 0);
     if (fac_bytes > 48 * 1024) {
         cudaError_t ea = cudaFuncSetAttribute(k_g_factor<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fac_bytes);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(k_g_refine_solve<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fac_bytes);
         if (ea != cudaSuccess) return hc_cuda_fail(ea, "k_g_factor shared memory");
     }
     cudaGraph_t graph = nullptr;
@@ -346,7 +356,7 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
         k_g_factor<L><<<1, HC_TB, fac_bytes, cs>>>(a, b_smem);
         for (int r = 0; r < max_refine; r++) {
             k_g_refine_rows<L><<<a.S.n, 32, 0, cs>>>(a);
-            k_g_refine_solve<L><<<1, HC_TB, ysh_bytes, cs>>>(a);
+            k_g_refine_solve<L><<<1, HC_TB, fac_bytes, cs>>>(a, b_smem);
         }
         k_g_update<L><<<1, HC_TB, 0, cs>>>(a);
     }
