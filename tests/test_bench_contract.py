@@ -38,3 +38,13 @@ def test_gpu_arm_refuses_to_run_without_a_gpu():
     r = _run(["--steps", "1", "--warmup", "0", "--no-extras"], timeout=120)
     assert r.returncode != 0
     assert "CUDA" in (r.stderr + r.stdout)
+
+
+def test_binding_fails_loudly_without_the_library():
+    """hc.load raises when libhc.so is absent (no CPU fallback exists)."""
+    code = ("from paper_1109_0545_gb300 import build, hc\n"
+            "build.SO = '/nonexistent/libhc.so'\n"
+            "hc.load(build_if_missing=False)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "libhc.so not built" in r.stderr
