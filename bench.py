@@ -644,6 +644,9 @@ def run_gpu(args):
                 "kernel": "k_eval_pts<DD,jacobian>", "ops_per_point": ops_pt,
                 "kernel_ms": eval_avg_ms, "traffic": captured_traffic(npts),
                 "traffic_note": "ncu dram read+write per launch, 8,192-point capture scaled by points"}
+    if roofline["traffic"] and eval_avg_ms > 0:
+        # the secondary counter: DRAM bytes per second of the evaluation kernel (the HBM is idle)
+        roofline["hbm_gbs"] = roofline["traffic"] / (eval_avg_ms * 1e-3) / 1e9
 
     extras = {}
     # the secondary measurements are single-GPU figures: with several ranks they would hold
