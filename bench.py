@@ -298,6 +298,34 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
     return out
 
 
+def single_path_bench(torch, hc, synth):
+    """The single-path workload (n = 8, 8 polynomials of 12 monomials plus a constant, k = 3,
+    exponents 1..3, complex DD, seed 1) on one block: the plain tracker (all-DD elimination,
+    secant predictor) and the FP64-LU tracker with the quadratic predictor.  Path steps
+    (corrector stages) per second and microseconds per stage; the end point's agreement with
+    the oracle is checked in tests/test_gpu_track.py."""
+    import numpy as np
+    s, g = synth.single_path_dd(1)
+    h = hc.system_from(s, 2, g)
+    out = {"n": s.n, "monomials": s.nmon}
+    for name, kw in (("plain_all_dd_secant", dict(lu_mode=hc.HC_LU_NATIVE)),
+                     ("fp64_refine_quadratic", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC))):
+        x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 2)])).cuda()
+        x1 = torch.zeros_like(x0)
+        o = hc.hc_track_opts_default(**kw)
+        hc.hc_track_path([h], x0, x1, o)            # warm-up (module load, allocations)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = hc.hc_track_path([h], x0, x1, o)[0]
+        dt = time.perf_counter() - t0
+        out[name] = {"status": hc.STATUS_NAMES[st["status"]], "stages": int(st["n_corr"]),
+                     "accepted": int(st["n_succ"]), "newton_its": int(st["newton_its"]),
+                     "path_steps_per_s": st["n_corr"] / dt, "us_per_step": 1e6 * dt / max(st["n_corr"], 1),
+                     "seconds": dt}
+    h.free()
+    return out
+
+
 def paper_tables_bench(torch, hc, synth):
     """One-path runs in complex QD (the paper's precision) on the shapes of its one-path
     experiments, regular variant (a constant and x_i^(D+1) added per polynomial so that the
@@ -700,6 +728,7 @@ def run_gpu(args):
             del xl, rl, sl, wl
         del xq
         extras = {"tracker": tracker_bench(torch, hc, synth, peak_gops, full_uneven=args.full_uneven),
+                  "single_path_n8": single_path_bench(torch, hc, synth),
                   "paper_tables": paper_tables_bench(torch, hc, synth),
                   "common_support_table1": common_support_bench(torch, hc, synth, peak_gops),
                   "quality_up": quality_up_bench(torch, hc, synth),
