@@ -10,5 +10,6 @@ split into limbs -- x[p][j][2][L], f[p][i][2][L], J[p][i][j][2][L], coef[m][2][L
 """
 from .wrap import (  # noqa: F401
     build, lib, r_add, r_mul, r_div, c_mul, c_div, degrees, validate, evaluate,
-    evaluate_threads, solve, newton_step, newton_threads, track, track_replay, TrackOpts, STATUS,
+    evaluate_threads, solve, newton_step, newton_threads, track, track_replay, track_resume, predict,
+    TrackOpts, PathState, STATUS,
 )

@@ -25,12 +25,18 @@
  *     parameter, not a variable (Sec. 7, Table 6 caption);
  *   - Gaussian elimination with partial pivoting on [A b] and back substitution (Sec. 4);
  *   - one Newton step (Alg. 4.1), native or FP64 LU with L-limb refinement;
- *   - the path tracker loop of Alg. 3.1 with a secant or quadratic (Sec. 5) predictor.
+ *   - the path tracker loop of Alg. 3.1 with a secant or quadratic (Sec. 5) predictor,
+ *     from t = 0 (or_track), from a saved state for a bounded number of stages
+ *     (or_track_resume), or along a given sequence of accepted t (or_track_replay); the
+ *     three share one implementation of each stage's steps.
  *
- * Pins (tests/test_oracle_pins.py) tie each routine to exact rationals, sympy, mpmath or
- * closed forms.  Parity unpinned: the exact stage-by-stage trajectory of or_track for
- * n > 1.  Only its invariants (steps on the lambda0 2^-j lattice, accepted steps adding up
- * to 1), its univariate end points and the start-system roots are pinned.
+ * Pins (tests/test_oracle_pins.py, tests/test_oracle_tracker_pins.py) tie each routine to
+ * exact rationals, sympy, mpmath or closed forms: the predictors to exact polynomial
+ * interpolation, the tracker to homotopies whose paths are exactly linear or quadratic
+ * in t, the homotopy at 0 < t < 1 to mpmath.  Parity unpinned: the exact stage-by-stage
+ * trajectory of or_track on a general system with n > 1.  Only its invariants (steps on
+ * the lambda0 2^-j lattice, accepted steps adding up to 1), its univariate end points,
+ * the constructed paths and the start-system roots are pinned.
  *
  * Readings of the paper where it is silent or garbled are stated at each routine.
  * Layout of every array here is point-major, array-of-structures:
@@ -978,6 +984,10 @@ int or_newton_step(int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr,
  * Predictors: 0 secant (linear through the last two accepted points; zeroth order when
  * there is only one), 1 quadratic (Sec. 5: per coordinate, the parabola through the
  * last three accepted points, evaluated at t'; lower order while fewer exist).
+ *
+ * The loop is split into the steps the three drivers share: or_track (from t = 0 to the
+ * end), or_track_resume (at most a given number of stages from a saved state) and
+ * or_track_replay (along a given sequence of accepted t values).
  * ---------------------------------------------------------------------------------- */
 typedef struct {
     double lambda0, lambda_min, lambda_max, grow, shrink;
@@ -997,6 +1007,16 @@ typedef struct {
     int32_t iters, accepted;
 } or_steplog;
 
+/* The state of a path between corrector stages: the current point's t and the two
+ * accepted values before it, the next step, the step controller's counters and the
+ * statistics of Tables 2-3.  phase: 1 tracking, 2 at t = 1 with the end game to run,
+ * 3 done.  The points themselves (z, z_prev, z_prev2) are held by the caller. */
+typedef struct {
+    double t, tp, tpp, lambda, min_step, sum_step, res_end;
+    int64_t n_succ, n_corr, newton_its;
+    int32_t nhist, consec, status, phase, end_its, pad;
+} or_state;
+
 static double cnorm_inf_lead(int n, const C *z)
 {
     double m = 0.0;
@@ -1007,139 +1027,307 @@ static double cnorm_inf_lead(int n, const C *z)
     return sqrt(m);
 }
 
+static void state_init(or_state *st, const or_opts *o)
+{
+    memset(st, 0, sizeof *st);
+    st->lambda = o->lambda0;
+    st->min_step = INFINITY;
+    st->res_end = -1.0;
+    st->nhist = 1;
+    st->status = OR_OK;
+    st->phase = 1;
+}
+
+/* Predictor (Alg. 3.1 "predict"; Sec. 5 for the quadratic one): the predicted point zh
+ * at t1 from the accepted points z (at t), zp (at tp) and zpp (at tpp), of which the
+ * first nhist exist.  Quadratic: the Lagrange form of the parabola through the three,
+ * its weights w0, w1, w2 formed in double; secant: z + (z - zp) (t1 - t) / (t - tp);
+ * zeroth order: z.  Each product of a point with a double weight is rounded once. */
+static void predict(int L, int n, int predictor, int nhist, double t, double tp, double tpp,
+                    double t1, const C *z, const C *zp, const C *zpp, C *zh)
+{
+    if (predictor == 1 && nhist >= 3) {
+        double w0 = ((t1 - tp) * (t1 - t)) / ((tpp - tp) * (tpp - t));
+        double w1 = ((t1 - tpp) * (t1 - t)) / ((tp - tpp) * (tp - t));
+        double w2 = ((t1 - tpp) * (t1 - tp)) / ((t - tpp) * (t - tp));
+        for (int j = 0; j < n; j++) {
+            C a = c_mul_r(L, zpp[j], r_from_d(w0));
+            C b = c_mul_r(L, zp[j], r_from_d(w1));
+            C c = c_mul_r(L, z[j], r_from_d(w2));
+            zh[j] = c_add(L, c_add(L, a, b), c);
+        }
+    } else if (nhist >= 2) {
+        double r = (t1 - t) / (t - tp);
+        for (int j = 0; j < n; j++)
+            zh[j] = c_add(L, z[j], c_mul_r(L, c_sub(L, z[j], zp[j]), r_from_d(r)));
+    } else {
+        memcpy(zh, z, sizeof(C) * (size_t)n);
+    }
+}
+
+/* exported predictor: points are [n][2][L]; returns -1 on a bad argument */
+int or_predict(int L, int n, int predictor, int nhist, double t, double tp, double tpp,
+               double t1, const double *z, const double *zp, const double *zpp, double *zh)
+{
+    if (!valid_L(L) || n < 1 || nhist < 1 || nhist > 3) return -1;
+    C *buf = (C *)malloc(sizeof(C) * (size_t)n * 4);
+    C *a = buf, *b = buf + n, *c = buf + 2 * (size_t)n, *out = buf + 3 * (size_t)n;
+    for (int j = 0; j < n; j++) {
+        a[j] = c_load(L, z + (size_t)j * 2 * L);
+        b[j] = c_load(L, zp + (size_t)j * 2 * L);
+        c[j] = c_load(L, zpp + (size_t)j * 2 * L);
+    }
+    predict(L, n, predictor, nhist, t, tp, tpp, t1, a, b, c, out);
+    for (int j = 0; j < n; j++) c_store(L, out[j], zh + (size_t)j * 2 * L);
+    free(buf);
+    return 0;
+}
+
+/* scratch of one path */
+typedef struct {
+    C *zh, *fv, *Jv, *M, *dz;
+} or_work;
+
+static void work_alloc(or_work *w, int n)
+{
+    size_t nc = (size_t)n;
+    w->zh = (C *)malloc(sizeof(C) * nc);
+    w->fv = (C *)malloc(sizeof(C) * nc);
+    w->Jv = (C *)malloc(sizeof(C) * nc * nc);
+    w->M = (C *)malloc(sizeof(C) * nc * (nc + 1));
+    w->dz = (C *)malloc(sizeof(C) * nc);
+}
+
+static void work_free(or_work *w)
+{
+    free(w->zh); free(w->fv); free(w->Jv); free(w->M); free(w->dz);
+}
+
+/* Corrector (Alg. 4.1) at t1 on zh in place: at most max_it Newton iterations until
+ * ||h||_inf <= eps or the update just applied has ||dz||_inf <= eps_x max(1, ||z||_inf).
+ * Returns the status of the last iteration; *its, *conv, *res (residual of the last
+ * iterate evaluated) and *res_first (of the first) as outputs. */
+static int correct(int L, const sysdesc *s, const int32_t *deg, C gam, const or_opts *o,
+                   double t1, int max_it, double eps, double eps_x, or_work *w, int *its,
+                   int *conv, double *res, double *res_first)
+{
+    int nst = OR_OK;
+    *its = 0;
+    *conv = 0;
+    *res = 1.0;
+    *res_first = -1.0;
+    while (!*conv && *its < max_it) {
+        int sw;
+        double dzn = 0.0, zn = 0.0;
+        nst = newton_once(L, s, deg, t1, gam, w->zh, o->lu_mode, o->max_refine, res, &sw, w->fv,
+                          w->Jv, w->M, w->dz, &dzn, &zn);
+        if (*res_first < 0) *res_first = *res;
+        (*its)++;
+        if (nst != OR_OK) break;
+        *conv = (*res <= eps) || (dzn <= eps_x * (zn > 1.0 ? zn : 1.0));
+    }
+    return nst;
+}
+
+/* Accept the corrected point zh at t1: shift the history (z -> zp -> zpp), t's, counts. */
+static void accept_point(or_state *st, int n, C *z, C *zp, C *zpp, const C *zh, double t1)
+{
+    size_t b = sizeof(C) * (size_t)n;
+    double h = t1 - st->t;
+    memcpy(zpp, zp, b);
+    memcpy(zp, z, b);
+    memcpy(z, zh, b);
+    st->tpp = st->tp;
+    st->tp = st->t;
+    st->t = t1;
+    if (st->nhist < 3) st->nhist++;
+    st->n_succ++;
+    st->sum_step += h;
+    if (h < st->min_step) st->min_step = h;
+}
+
+/* End game at t = 1: up to end_it Newton iterations on f; phase 2 -> 3. */
+static void end_game(int L, const sysdesc *s, const int32_t *deg, C gam, const or_opts *o,
+                     or_state *st, C *z, or_work *w)
+{
+    int n = s->n, its, conv;
+    double res, res_first;
+    memcpy(w->zh, z, sizeof(C) * (size_t)n);
+    int nst = correct(L, s, deg, gam, o, 1.0, o->end_it, o->eps_end, o->eps_end_x, w, &its, &conv,
+                      &res, &res_first);
+    /* every iteration that ran moved z (an iteration that failed left zh unchanged) */
+    memcpy(z, w->zh, sizeof(C) * (size_t)n);
+    st->end_its += its;
+    st->res_end = res;
+    if (nst != OR_OK) st->status = nst;
+    else if (!conv) st->status = OR_NOCONV;
+    st->phase = 3;
+}
+
+/* One corrector stage of Alg. 3.1 from state st (phase 1): predict, correct, accept or
+ * step back, step-size control, stop tests; the log record if asked for. */
+static void stage(int L, const sysdesc *s, const int32_t *deg, C gam, const or_opts *o,
+                  or_state *st, C *z, C *zp, C *zpp, or_work *w, or_steplog *log, int log_cap,
+                  int32_t *nl)
+{
+    int n = s->n;
+    double t1 = st->t + st->lambda;
+    if (t1 > 1.0) t1 = 1.0;
+    double h = t1 - st->t;
+    predict(L, n, o->predictor, st->nhist, st->t, st->tp, st->tpp, t1, z, zp, zpp, w->zh);
+    int its, conv;
+    double res, res_first;
+    int nst = correct(L, s, deg, gam, o, t1, o->max_it, o->eps, o->eps_x, w, &its, &conv, &res,
+                      &res_first);
+    st->newton_its += its;
+    st->n_corr++;
+    int ok = (nst == OR_OK) && conv, stop = 0;
+    double znorm = cnorm_inf_lead(n, w->zh);
+    if (ok && !(znorm <= o->div_bound)) {
+        ok = 0;
+        st->status = isfinite(znorm) ? OR_DIVERGED : OR_NONFINITE;
+        stop = 1;
+    }
+    if (log && *nl < log_cap) {
+        /* the distance between the predicted and the corrected point is not logged */
+        or_steplog *rec = &log[(*nl)++];
+        rec->t = st->t;
+        rec->lambda = h;
+        rec->res_first = res_first;
+        rec->res_last = res;
+        rec->iters = its;
+        rec->accepted = ok;
+        rec->pc_dist = -1.0;
+    }
+    if (ok) {
+        accept_point(st, n, z, zp, zpp, w->zh, t1);
+        st->consec++;
+        if (st->consec >= o->grow_after) {
+            st->lambda = st->lambda * o->grow;
+            if (st->lambda > o->lambda_max) st->lambda = o->lambda_max;
+            st->consec = 0;
+        }
+    } else if (!stop) {
+        st->consec = 0;
+        st->lambda = st->lambda * o->shrink;
+        if (st->lambda < o->lambda_min) { stop = 1; st->status = OR_MIN_STEP; }
+    }
+    if (!stop && st->t < 1.0 && st->n_corr >= o->max_steps) { stop = 1; st->status = OR_MAX_STEPS; }
+    if (stop) st->phase = 3;
+    else if (st->t >= 1.0) st->phase = 2;
+}
+
+/* At most max_stages corrector stages from st, then the end game if t = 1 was reached. */
+static void run_stages(int L, const sysdesc *s, const int32_t *deg, C gam, const or_opts *o,
+                       or_state *st, C *z, C *zp, C *zpp, int64_t max_stages, or_steplog *log,
+                       int32_t *nl)
+{
+    or_work w;
+    work_alloc(&w, s->n);
+    for (int64_t k = 0; st->phase == 1 && k < max_stages; k++)
+        stage(L, s, deg, gam, o, st, z, zp, zpp, &w, log, o->log_cap, nl);
+    if (st->phase == 2) end_game(L, s, deg, gam, o, st, z, &w);
+    work_free(&w);
+}
+
+static void stats_of(const or_state *st, or_stats *out)
+{
+    out->n_succ = st->n_succ;
+    out->n_corr = st->n_corr;
+    out->newton_its = st->newton_its;
+    out->min_step = st->n_succ ? st->min_step : 0.0;
+    out->avg_step = st->n_succ ? st->sum_step / (double)st->n_succ : 0.0;
+    out->t_end = st->t;
+    out->res_end = st->res_end;
+    out->status = st->status;
+    out->end_its = st->end_its;
+}
+
+typedef struct {
+    sysdesc s;
+    int32_t *deg;
+    C gam, *z, *zp, *zpp;
+} or_path;
+
+static int path_open(or_path *p, int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr,
+                     const int32_t *var_idx, const int32_t *var_exp, const double *coef,
+                     const double *gamma)
+{
+    if (!valid_L(L)) return -1;
+    if (or_validate(n, n, mon_ptr, var_ptr, var_idx, var_exp) != 0) return -2;
+    sysdesc s = {n, n, mon_ptr, var_ptr, var_idx, var_exp, coef};
+    p->s = s;
+    p->deg = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    or_degrees(n, mon_ptr, var_ptr, var_exp, p->deg);
+    p->gam = c_from(gamma[0], gamma[1]);
+    p->z = (C *)calloc((size_t)n, sizeof(C));
+    p->zp = (C *)calloc((size_t)n, sizeof(C));
+    p->zpp = (C *)calloc((size_t)n, sizeof(C));
+    return 0;
+}
+
+static void path_close(or_path *p)
+{
+    free(p->deg); free(p->z); free(p->zp); free(p->zpp);
+}
+
+static void load_vec(int L, int n, const double *src, C *dst)
+{
+    for (int j = 0; j < n; j++) dst[j] = c_load(L, src + (size_t)j * 2 * L);
+}
+
+static void store_vec(int L, int n, const C *src, double *dst)
+{
+    for (int j = 0; j < n; j++) c_store(L, src[j], dst + (size_t)j * 2 * L);
+}
+
+/* or_track: one path from x0 at t = 0 to its end (Alg. 3.1).  x0, x1 are [n][2][L]; x1
+ * gets the last accepted point (the end point if the status is OK). */
 int or_track(int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr,
              const int32_t *var_idx, const int32_t *var_exp, const double *coef,
              const double *gamma, const double *x0, const or_opts *o, double *x1,
              or_stats *st, or_steplog *log, int32_t *nlog)
 {
-    if (!valid_L(L)) return -1;
-    if (or_validate(n, n, mon_ptr, var_ptr, var_idx, var_exp) != 0) return -2;
-    sysdesc s = {n, n, mon_ptr, var_ptr, var_idx, var_exp, coef};
-    int32_t *deg = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    or_degrees(n, mon_ptr, var_ptr, var_exp, deg);
-    C gam = c_from(gamma[0], gamma[1]);
-    size_t nc = (size_t)n;
-    C *z = (C *)malloc(sizeof(C) * nc), *zp = (C *)malloc(sizeof(C) * nc);
-    C *zpp = (C *)malloc(sizeof(C) * nc), *zh = (C *)malloc(sizeof(C) * nc);
-    C *fv = (C *)malloc(sizeof(C) * nc), *Jv = (C *)malloc(sizeof(C) * nc * nc);
-    C *M = (C *)malloc(sizeof(C) * nc * (nc + 1)), *dz = (C *)malloc(sizeof(C) * nc);
-    for (int j = 0; j < n; j++) z[j] = c_load(L, x0 + (size_t)j * 2 * L);
-    double t = 0.0, tp = 0.0, tpp = 0.0, lambda = o->lambda0;
-    int nhist = 1; /* accepted points available: z (and zp, zpp) */
-    int consec = 0, status = OR_OK, stop = 0;
-    int64_t nsucc = 0, ncorr = 0, nits = 0;
-    double minstep = INFINITY, sumstep = 0.0;
+    or_path p;
+    int rc = path_open(&p, L, n, mon_ptr, var_ptr, var_idx, var_exp, coef, gamma);
+    if (rc) return rc;
+    or_state s;
+    state_init(&s, o);
+    load_vec(L, n, x0, p.z);
     int32_t nl = 0;
-    while (t < 1.0 && !stop) {
-        double t1 = t + lambda;
-        if (t1 > 1.0) t1 = 1.0;
-        double h = t1 - t;
-        /* predictor */
-        if (o->predictor == 1 && nhist >= 3) {
-            /* Lagrange weights of the parabola through (tpp,zpp), (tp,zp), (t,z) at t1 */
-            double w0 = ((t1 - tp) * (t1 - t)) / ((tpp - tp) * (tpp - t));
-            double w1 = ((t1 - tpp) * (t1 - t)) / ((tp - tpp) * (tp - t));
-            double w2 = ((t1 - tpp) * (t1 - tp)) / ((t - tpp) * (t - tp));
-            for (int j = 0; j < n; j++) {
-                C a = c_mul_r(L, zpp[j], r_from_d(w0));
-                C b = c_mul_r(L, zp[j], r_from_d(w1));
-                C c = c_mul_r(L, z[j], r_from_d(w2));
-                zh[j] = c_add(L, c_add(L, a, b), c);
-            }
-        } else if (nhist >= 2) {
-            double r = h / (t - tp);
-            for (int j = 0; j < n; j++)
-                zh[j] = c_add(L, z[j], c_mul_r(L, c_sub(L, z[j], zp[j]), r_from_d(r)));
-        } else {
-            memcpy(zh, z, sizeof(C) * nc);
-        }
-        /* corrector: Alg. 4.1 */
-        double res = 1.0, res_first = -1.0, dzn = 0.0, zn = 0.0;
-        int it = 0, nst = OR_OK, conv = 0;
-        while (!conv && it < o->max_it) {
-            int sw;
-            nst = newton_once(L, &s, deg, t1, gam, zh, o->lu_mode, o->max_refine, &res, &sw, fv, Jv,
-                              M, dz, &dzn, &zn);
-            if (res_first < 0) res_first = res;
-            it++;
-            if (nst != OR_OK) break;
-            conv = (res <= o->eps) || (dzn <= o->eps_x * (zn > 1.0 ? zn : 1.0));
-        }
-        nits += it;
-        ncorr++;
-        int ok = (nst == OR_OK) && conv;
-        double znorm = cnorm_inf_lead(n, zh);
-        if (ok && !(znorm <= o->div_bound)) {
-            ok = 0;
-            status = isfinite(znorm) ? OR_DIVERGED : OR_NONFINITE;
-            stop = 1;
-        }
-        if (log && nl < o->log_cap) {
-            /* distance between the predicted and the corrected point is measured on
-               the accepted branch only; on failure it is left at -1 */
-            or_steplog *rec = &log[nl++];
-            rec->t = t;
-            rec->lambda = h;
-            rec->res_first = res_first;
-            rec->res_last = res;
-            rec->iters = it;
-            rec->accepted = ok;
-            rec->pc_dist = -1.0;
-        }
-        if (ok) {
-            memcpy(zpp, zp, sizeof(C) * nc);
-            memcpy(zp, z, sizeof(C) * nc);
-            memcpy(z, zh, sizeof(C) * nc);
-            tpp = tp;
-            tp = t;
-            t = t1;
-            if (nhist < 3) nhist++;
-            nsucc++;
-            sumstep += h;
-            if (h < minstep) minstep = h;
-            consec++;
-            if (consec >= o->grow_after) {
-                lambda = lambda * o->grow;
-                if (lambda > o->lambda_max) lambda = o->lambda_max;
-                consec = 0;
-            }
-        } else if (!stop) {
-            consec = 0;
-            lambda = lambda * o->shrink;
-            if (lambda < o->lambda_min) { stop = 1; status = OR_MIN_STEP; }
-        }
-        if (!stop && t < 1.0 && ncorr >= o->max_steps) { stop = 1; status = OR_MAX_STEPS; }
-    }
-    double res_end = -1.0;
-    int end_its = 0;
-    if (t >= 1.0 && status == OR_OK) {
-        double res = 1.0, dzn = 0.0, zn = 0.0;
-        int conv = 0;
-        while (!conv && end_its < o->end_it) {
-            int sw;
-            int nst = newton_once(L, &s, deg, 1.0, gam, z, o->lu_mode, o->max_refine, &res, &sw, fv,
-                                  Jv, M, dz, &dzn, &zn);
-            end_its++;
-            if (nst != OR_OK) { status = nst; break; }
-            conv = (res <= o->eps_end) || (dzn <= o->eps_end_x * (zn > 1.0 ? zn : 1.0));
-        }
-        res_end = res;
-        if (status == OR_OK && !conv) status = OR_NOCONV;
-    }
-    for (int j = 0; j < n; j++) c_store(L, z[j], x1 + (size_t)j * 2 * L);
-    if (st) {
-        st->n_succ = nsucc;
-        st->n_corr = ncorr;
-        st->newton_its = nits;
-        st->min_step = nsucc ? minstep : 0.0;
-        st->avg_step = nsucc ? sumstep / (double)nsucc : 0.0;
-        st->t_end = t;
-        st->res_end = res_end;
-        st->status = status;
-        st->end_its = end_its;
-    }
+    run_stages(L, &p.s, p.deg, p.gam, o, &s, p.z, p.zp, p.zpp, INT64_MAX, log, &nl);
+    store_vec(L, n, p.z, x1);
+    if (st) stats_of(&s, st);
     if (nlog) *nlog = nl;
-    free(deg); free(z); free(zp); free(zpp); free(zh); free(fv); free(Jv); free(M); free(dz);
+    path_close(&p);
+    return 0;
+}
+
+/* or_track_resume: at most max_stages corrector stages of one path from a saved state
+ * (then the end game if t = 1 is reached), the state saved again.  state->phase == 0
+ * starts the path at t = 0 from z.  z, zp, zpp: [n][2][L] in/out, the current point and
+ * the two accepted points before it (the first state->nhist of the three are used). */
+int or_track_resume(int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr,
+                    const int32_t *var_idx, const int32_t *var_exp, const double *coef,
+                    const double *gamma, const or_opts *o, or_state *state, double *z,
+                    double *zp, double *zpp, int64_t max_stages, or_stats *st,
+                    or_steplog *log, int32_t *nlog)
+{
+    or_path p;
+    int rc = path_open(&p, L, n, mon_ptr, var_ptr, var_idx, var_exp, coef, gamma);
+    if (rc) return rc;
+    if (state->phase == 0) state_init(state, o);
+    load_vec(L, n, z, p.z);
+    load_vec(L, n, zp, p.zp);
+    load_vec(L, n, zpp, p.zpp);
+    int32_t nl = 0;
+    run_stages(L, &p.s, p.deg, p.gam, o, state, p.z, p.zp, p.zpp, max_stages, log, &nl);
+    store_vec(L, n, p.z, z);
+    store_vec(L, n, p.zp, zp);
+    store_vec(L, n, p.zpp, zpp);
+    if (st) stats_of(state, st);
+    if (nlog) *nlog = nl;
+    path_close(&p);
     return 0;
 }
 
@@ -1155,96 +1343,39 @@ int or_track_replay(int L, int n, const int32_t *mon_ptr, const int32_t *var_ptr
                     const double *gamma, const double *x0, const or_opts *o, const double *tseq,
                     int nseq, double *x1, int32_t *fail_at, or_stats *st)
 {
-    if (!valid_L(L)) return -1;
-    if (or_validate(n, n, mon_ptr, var_ptr, var_idx, var_exp) != 0) return -2;
-    sysdesc s = {n, n, mon_ptr, var_ptr, var_idx, var_exp, coef};
-    int32_t *deg = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    or_degrees(n, mon_ptr, var_ptr, var_exp, deg);
-    C gam = c_from(gamma[0], gamma[1]);
-    size_t nc = (size_t)n;
-    C *z = (C *)malloc(sizeof(C) * nc), *zp = (C *)malloc(sizeof(C) * nc);
-    C *zpp = (C *)malloc(sizeof(C) * nc), *zh = (C *)malloc(sizeof(C) * nc);
-    C *fv = (C *)malloc(sizeof(C) * nc), *Jv = (C *)malloc(sizeof(C) * nc * nc);
-    C *M = (C *)malloc(sizeof(C) * nc * (nc + 1)), *dz = (C *)malloc(sizeof(C) * nc);
-    for (int j = 0; j < n; j++) z[j] = c_load(L, x0 + (size_t)j * 2 * L);
-    double t = 0.0, tp = 0.0, tpp = 0.0;
-    int nhist = 1, status = OR_OK;
+    or_path p;
+    int rc = path_open(&p, L, n, mon_ptr, var_ptr, var_idx, var_exp, coef, gamma);
+    if (rc) return rc;
+    or_state s;
+    state_init(&s, o);
+    load_vec(L, n, x0, p.z);
+    or_work w;
+    work_alloc(&w, n);
     *fail_at = -1;
-    int64_t nits = 0;
     for (int k = 0; k < nseq; k++) {
         double t1 = tseq[k];
-        double h = t1 - t;
-        if (o->predictor == 1 && nhist >= 3) {
-            double w0 = ((t1 - tp) * (t1 - t)) / ((tpp - tp) * (tpp - t));
-            double w1 = ((t1 - tpp) * (t1 - t)) / ((tp - tpp) * (tp - t));
-            double w2 = ((t1 - tpp) * (t1 - tp)) / ((t - tpp) * (t - tp));
-            for (int j = 0; j < n; j++) {
-                C a = c_mul_r(L, zpp[j], r_from_d(w0));
-                C b = c_mul_r(L, zp[j], r_from_d(w1));
-                C c = c_mul_r(L, z[j], r_from_d(w2));
-                zh[j] = c_add(L, c_add(L, a, b), c);
-            }
-        } else if (nhist >= 2) {
-            double r = h / (t - tp);
-            for (int j = 0; j < n; j++)
-                zh[j] = c_add(L, z[j], c_mul_r(L, c_sub(L, z[j], zp[j]), r_from_d(r)));
-        } else {
-            memcpy(zh, z, sizeof(C) * nc);
-        }
-        double res = 1.0, dzn = 0.0, zn = 0.0;
-        int it = 0, nst = OR_OK, conv = 0;
-        while (!conv && it < o->max_it) {
-            int sw;
-            nst = newton_once(L, &s, deg, t1, gam, zh, o->lu_mode, o->max_refine, &res, &sw, fv, Jv,
-                              M, dz, &dzn, &zn);
-            it++;
-            if (nst != OR_OK) break;
-            conv = (res <= o->eps) || (dzn <= o->eps_x * (zn > 1.0 ? zn : 1.0));
-        }
-        nits += it;
+        predict(L, n, o->predictor, s.nhist, s.t, s.tp, s.tpp, t1, p.z, p.zp, p.zpp, w.zh);
+        int its, conv;
+        double res, res_first;
+        int nst = correct(L, &p.s, p.deg, p.gam, o, t1, o->max_it, o->eps, o->eps_x, &w, &its,
+                          &conv, &res, &res_first);
+        s.newton_its += its;
+        s.n_corr++;
         if (!(nst == OR_OK && conv)) {
             *fail_at = k;
-            status = OR_NOCONV;
+            s.status = OR_NOCONV;
+            s.phase = 3;
             break;
         }
-        memcpy(zpp, zp, sizeof(C) * nc);
-        memcpy(zp, z, sizeof(C) * nc);
-        memcpy(z, zh, sizeof(C) * nc);
-        tpp = tp;
-        tp = t;
-        t = t1;
-        if (nhist < 3) nhist++;
+        accept_point(&s, n, p.z, p.zp, p.zpp, w.zh, t1);
     }
-    double res_end = -1.0;
-    int end_its = 0;
-    if (status == OR_OK && t >= 1.0) {
-        double res = 1.0, dzn = 0.0, zn = 0.0;
-        int conv = 0;
-        while (!conv && end_its < o->end_it) {
-            int sw;
-            int nst = newton_once(L, &s, deg, 1.0, gam, z, o->lu_mode, o->max_refine, &res, &sw, fv,
-                                  Jv, M, dz, &dzn, &zn);
-            end_its++;
-            if (nst != OR_OK) { status = nst; break; }
-            conv = (res <= o->eps_end) || (dzn <= o->eps_end_x * (zn > 1.0 ? zn : 1.0));
-        }
-        res_end = res;
-        if (status == OR_OK && !conv) status = OR_NOCONV;
-    }
-    for (int j = 0; j < n; j++) c_store(L, z[j], x1 + (size_t)j * 2 * L);
-    if (st) {
-        memset(st, 0, sizeof *st);
-        st->n_succ = nseq;
-        st->newton_its = nits;
-        st->t_end = t;
-        st->res_end = res_end;
-        st->status = status;
-        st->end_its = end_its;
-    }
-    free(deg); free(z); free(zp); free(zpp); free(zh); free(fv); free(Jv); free(M); free(dz);
+    if (s.phase == 1 && s.t >= 1.0) end_game(L, &p.s, p.deg, p.gam, o, &s, p.z, &w);
+    work_free(&w);
+    store_vec(L, n, p.z, x1);
+    if (st) stats_of(&s, st);
+    path_close(&p);
     return 0;
 }
-
 /* ------------------------------------------------------------------------------------
  * Threaded batch driver for the CPU baseline: or_eval (mode 1) over points on nthreads
  * POSIX threads, each thread a contiguous block of points.

@@ -58,6 +58,17 @@ class _Stats(ct.Structure):
                 ("res_end", ct.c_double), ("status", ct.c_int32), ("end_its", ct.c_int32)]
 
 
+class PathState(ct.Structure):
+    """The oracle's state of a path between corrector stages (or_state in hc_oracle.c);
+    phase 0 starts the path at t = 0, 1 tracking, 2 end game pending, 3 done."""
+    _fields_ = [("t", ct.c_double), ("tp", ct.c_double), ("tpp", ct.c_double),
+                ("lam", ct.c_double), ("min_step", ct.c_double), ("sum_step", ct.c_double),
+                ("res_end", ct.c_double), ("n_succ", ct.c_int64), ("n_corr", ct.c_int64),
+                ("newton_its", ct.c_int64), ("nhist", ct.c_int32), ("consec", ct.c_int32),
+                ("status", ct.c_int32), ("phase", ct.c_int32), ("end_its", ct.c_int32),
+                ("pad", ct.c_int32)]
+
+
 class _StepLog(ct.Structure):
     _fields_ = [("t", ct.c_double), ("lam", ct.c_double), ("res_first", ct.c_double),
                 ("res_last", ct.c_double), ("pc_dist", ct.c_double), ("iters", ct.c_int32),
@@ -105,6 +116,13 @@ def lib():
                                           ct.POINTER(TrackOpts), _F64P, i, _F64P,
                                           ct.POINTER(ct.c_int32), ct.POINTER(_Stats)]
             L.or_track_replay.restype = i
+            L.or_track_resume.argtypes = [i, i, _I32P, _I32P, _I32P, _I32P, _F64P, _F64P,
+                                          ct.POINTER(TrackOpts), ct.POINTER(PathState), _F64P,
+                                          _F64P, _F64P, ct.c_int64, ct.POINTER(_Stats), p,
+                                          ct.POINTER(ct.c_int32)]
+            L.or_track_resume.restype = i
+            L.or_predict.argtypes = [i, i, i, i, d, d, d, d, _F64P, _F64P, _F64P, _F64P]
+            L.or_predict.restype = i
             _lib = L
     return _lib
 
@@ -271,15 +289,57 @@ def track(sysd, coef, x0, gamma, opts: TrackOpts, log_cap=0):
                         ct.byref(nl))
     if rc != 0:
         raise ValueError(f"or_track failed ({rc})")
-    log = None
-    if log_cap:
-        log = np.array([(r.t, r.lam, r.res_first, r.res_last, r.pc_dist, r.iters, r.accepted)
-                        for r in logbuf[:nl.value]],
-                       dtype=[("t", "f8"), ("lam", "f8"), ("res_first", "f8"),
-                              ("res_last", "f8"), ("pc_dist", "f8"), ("iters", "i4"),
-                              ("accepted", "i4")])
+    log = _log_array(logbuf, nl.value) if log_cap else None
     return TrackResult(x1, st.status, st.n_succ, st.n_corr, st.newton_its, st.min_step,
                        st.avg_step, st.t_end, st.res_end, st.end_its, log)
+
+
+def _log_array(logbuf, count):
+    return np.array([(r.t, r.lam, r.res_first, r.res_last, r.pc_dist, r.iters, r.accepted)
+                     for r in logbuf[:count]],
+                    dtype=[("t", "f8"), ("lam", "f8"), ("res_first", "f8"), ("res_last", "f8"),
+                           ("pc_dist", "f8"), ("iters", "i4"), ("accepted", "i4")])
+
+
+def track_resume(sysd, coef, gamma, opts: TrackOpts, state: PathState, z, zp, zpp, max_stages,
+                 log_cap=0):
+    """At most max_stages corrector stages of one path from `state` (phase 0: start at
+    t = 0 from z), then the end game if t = 1 is reached.  z, zp, zpp: [n][2][L], the
+    current point and the two accepted points before it.  Returns (new state, z, zp, zpp,
+    statistics dict, log or None); the arguments are not modified."""
+    L = coef.shape[-1]
+    n = sysd["n"]
+    st = PathState()
+    ct.pointer(st)[0] = state
+    zz, zzp, zzpp = (_f64(v, (n, 2, L)).copy() for v in (z, zp, zpp))
+    stats = _Stats()
+    o = TrackOpts()
+    ct.pointer(o)[0] = opts
+    o.log_cap = int(log_cap)
+    logbuf = (_StepLog * max(1, log_cap))()
+    nl = ct.c_int32(0)
+    rc = lib().or_track_resume(L, n, *_sysargs(sysd), _f64(coef), _f64(gamma), ct.byref(o),
+                               ct.byref(st), zz, zzp, zzpp, int(max_stages), ct.byref(stats),
+                               ct.cast(logbuf, ct.c_void_p), ct.byref(nl))
+    if rc != 0:
+        raise ValueError(f"or_track_resume failed ({rc})")
+    sd = {k: getattr(stats, k) for k, _ in _Stats._fields_}
+    return st, zz, zzp, zzpp, sd, (_log_array(logbuf, nl.value) if log_cap else None)
+
+
+def predict(L, predictor, nhist, t, tp, tpp, t1, z, zp, zpp):
+    """The tracker's predictor (Alg. 3.1; Sec. 5 quadratic) at t1 from the accepted points
+    z (at t), zp (at tp), zpp (at tpp), each [n][2][L]; nhist of them exist.
+    predictor 0 secant, 1 quadratic."""
+    z = _f64(z)
+    n = z.shape[0]
+    out = np.zeros((n, 2, L))
+    rc = lib().or_predict(L, n, int(predictor), int(nhist), float(t), float(tp), float(tpp),
+                          float(t1), _f64(z, (n, 2, L)), _f64(zp, (n, 2, L)), _f64(zpp, (n, 2, L)),
+                          out)
+    if rc != 0:
+        raise ValueError(f"or_predict failed ({rc})")
+    return out
 
 
 def track_replay(sysd, coef, x0, gamma, opts: TrackOpts, tseq):
