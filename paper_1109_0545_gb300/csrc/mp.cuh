@@ -95,11 +95,10 @@ template <int L> __device__ __forceinline__ R<L> r_neg(R<L> a)
 }
 
 // ---------------------------------------------------------------- renormalisation (QD)
-// Five components of roughly decreasing magnitude -> four nonoverlapping limbs.
-// Bottom-up two-sums carry the value up exactly (two-sums, not fast-two-sums: after a
-// cancellation the components need not be ordered); the top-down fast-two-sums then
-// re-split it (a zero component bubbles down: fast_two_sum(0, b) = (b, 0)).  22 FP64.
-__device__ __forceinline__ R<4> renorm5(double c0, double c1, double c2, double c3, double c4)
+// Five components of roughly decreasing magnitude -> four limbs.  Bottom-up two-sums
+// carry the value up exactly (two-sums, not fast-two-sums: after a cancellation the
+// components need not be ordered); the top-down fast-two-sums then re-split it.  22 FP64.
+__device__ __forceinline__ R<4> renorm5_pass(double c0, double c1, double c2, double c3, double c4)
 {
     double s, t3, t2, t1, t0;
     two_sum_ord(c3, c4, s, t3);
@@ -112,6 +111,35 @@ __device__ __forceinline__ R<4> renorm5(double c0, double c1, double c2, double 
     fast_two_sum(e, t1, r.v[1], e);
     fast_two_sum(e, t2, r.v[2], e);
     r.v[3] = add_(e, t3);
+    return r;
+}
+
+// Biased exponent field of x (0 for zero and subnormals), on the INT pipe.
+__device__ __forceinline__ int exp_field(double x)
+{
+    return (int)(((unsigned)__double2hiint(x) << 1) >> 21);
+}
+
+// The limbs are nonoverlapping: each nonzero limb has an exponent at least 53 below the
+// one above it (so it is below a unit in the last place of that limb), and the leading
+// limb is the value to within a unit in its last place.  Integer comparisons only.
+__device__ __forceinline__ bool qd_separated(const R<4> &r)
+{
+    const int e0 = exp_field(r.v[0]), e1 = exp_field(r.v[1]), e2 = exp_field(r.v[2]), e3 = exp_field(r.v[3]);
+    return !((e1 && e1 + 53 > e0) || (e2 && e2 + 53 > e1) || (e3 && e3 + 53 > e2));
+}
+
+// Renormalisation.  When the components cancel at the top (say c0 + the sum of the rest
+// is zero or a few units in its last place, as in the difference of two nearly equal
+// values), one pass leaves the value in the lower limbs: the leading limb is zero or
+// much smaller than the next one, although the sum of the limbs is exact.  Code that
+// reads only the leading limb (norms, pivots, the right-hand side of an FP64
+// refinement solve) would then see the wrong value, so such a result takes a second
+// pass, whose input no longer cancels.  22 FP64 (44 in the rare second pass).
+__device__ __forceinline__ R<4> renorm5(double c0, double c1, double c2, double c3, double c4)
+{
+    R<4> r = renorm5_pass(c0, c1, c2, c3, c4);
+    if (!qd_separated(r)) r = renorm5_pass(r.v[0], r.v[1], r.v[2], r.v[3], 0.0);
     return r;
 }
 
