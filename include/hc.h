@@ -201,6 +201,40 @@ typedef struct {
     int32_t end_its;     /* Newton iterations of the end game */
 } hc_path_stats;
 
+/* The state of one path between corrector stages: what hc_track_resume saves and
+ * restarts from (checkpoint / resume; the paper has no such feature, its tracker keeps
+ * these values in the variables of Alg. 3.1).  The two accepted points before the
+ * current one live in the caller's hist buffer (see hc_track_resume).  A caller may
+ * inspect the state, store it, or change it between calls: e.g. to continue a path that
+ * stopped at HC_MAX_STEPS, raise opts->max_steps and set phase = 1, status = HC_OK. */
+typedef struct {
+    double t;          /* t of the current point (the last accepted one) */
+    double tp, tpp;    /* t of the two accepted points before it */
+    double lambda;     /* step of the next corrector stage */
+    double minstep;    /* smallest accepted step (+inf before the first) */
+    double sumstep;    /* sum of the accepted steps */
+    double res_end;    /* residual of the last end-game iteration, -1 before the end game */
+    double pad;
+    int64_t n_succ;    /* accepted corrector stages */
+    int64_t n_corr;    /* corrector stages */
+    int64_t nits;      /* Newton iterations of the stages */
+    int32_t nhist;     /* accepted points in the history (current one included): 1, 2, 3 */
+    int32_t consec;    /* consecutive accepted stages since the step last grew */
+    int32_t status;    /* HC_OK while the path runs; its final status once done */
+    int32_t phase;     /* 0: start at t = 0 from x; 1: tracking; 2: the end game is next;
+                          3: done */
+    int32_t end_its;   /* Newton iterations of the end game */
+    int32_t pad2;
+    double hl[3];      /* the last three attempted steps (latest first) } features of */
+    double hr[3];      /* their last residuals                           } the learned */
+    double pcd;        /* the last predictor-corrector distance (-1)     } step proposer */
+    double cond;       /* log10 condition estimate of the last factorisation */
+    int32_t hi[3];     /* Newton iterations of the last three stages */
+    int32_t pad3;
+    double lam_plain;  /* the plain controller's step, run alongside a proposer */
+    int64_t pid;       /* path index: the stream of the exploration generator */
+} hc_path_state;
+
 /* One corrector stage, as logged for the learned step-size proposer. */
 typedef struct {
     double t;            /* t before the stage */
@@ -263,6 +297,34 @@ int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x
                   int log_cap, void *stream);
 
 /*
+ * hc_track_resume -- checkpoint / resume of hc_track_path (Alg. 3.1): advance each path
+ * by at most max_stages corrector stages from its saved state, then run its end game if
+ * it reached t = 1, and save the state again.  Repeated calls with max_stages = k give
+ * the same paths, bit for bit, as one hc_track_path call (same options).
+ *   sys, opts  as for hc_track_path (every mode; the tangent predictor needs the tangent
+ *              of the history, so it resumes only from states this function wrote)
+ *   x      device, packed as hc_track_path's x0, in/out: on input the start point of a
+ *          path in phase 0, else its current point; on output its current point
+ *   hist   device, in/out, 3 vectors of 2 L n_p doubles per path, path p at offset
+ *          3 * 2 L (n_0 + ... + n_{p-1}): the accepted point before the current one and
+ *          the one before that ([2][L][n_p] each; the first state.nhist - 1 are used),
+ *          then dx/dt at the current point ([2][n_p] leading limbs in the first 2 n_p
+ *          doubles; written by the tangent predictor only).  Need not be initialised for
+ *          a path in phase 0.
+ *   state  host, npaths states in/out (phase 0: start the path at t = 0 from x; phase 3:
+ *          left as is)
+ *   max_stages  >= 1, corrector stages per path in this call
+ *   stats  host, npaths results as hc_track_path's (may be NULL)
+ *   log    device, npaths * log_cap records of this call's stages (record s of path p at
+ *          p * log_cap + s), or NULL with log_cap = 0
+ * Synchronises the stream before returning.  Allocates and frees its own workspace.
+ * Errors: HC_EINVAL (bad argument, an unknown phase), HC_ENOMEM, HC_ECUDA, HC_ETIMEOUT.
+ */
+int hc_track_resume(hc_system *const *sys, int npaths, double *x, double *hist,
+                    hc_path_state *state, int max_stages, const hc_track_opts *opts,
+                    hc_path_stats *stats, hc_step_record *log, int log_cap, void *stream);
+
+/*
  * The learned step-size proposer (not in the paper; the plain controller of Alg. 3.1
  * stays the fallback and the corrector still judges every step): a 12 -> 64 -> 64 -> 1
  * perceptron with GELU, bfloat16 operands, float32 accumulation and float32 master
@@ -284,9 +346,9 @@ int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x
 
 /* grad[HC_MLP_NPARAM] = gradient of the mean loss over nrec records (feat[nrec][12],
  * target[nrec] = r, accepted[nrec]); *loss = the mean loss (loss may be NULL).  The
- * summation order is fixed: results are reproducible bit for bit.  Keeps a process-wide
- * workspace of per-block partial gradients (grown on demand, synchronising): calls must
- * not overlap.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA. */
+ * summation order is fixed: results are reproducible bit for bit.  Keeps a workspace of
+ * per-block partial gradients for each device (grown on demand, synchronising): calls on
+ * one device must not overlap.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA. */
 int hc_mlp_grad(const float *params, int nrec, const float *feat, const float *target,
                 const int32_t *accepted, float kappa, float *grad, float *loss, void *stream);
 
@@ -327,7 +389,10 @@ int hc_probe_fp64_peak(double *gops);
  *     n = 32, exponents up to 4, DD.  Split larger point sets over several calls.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture.
+ *     stream capture.  The address is cached per device for the life of the process: a
+ *     cudaDeviceReset destroys the array with the context, so after a reset (which ends
+ *     every allocation of the process on that device anyway) this entry point must not
+ *     be called again on that device.
  *   - Every call uses the same array: calls whose kernels overlap on the GPU (other
  *     streams, other host threads) race on it, so serialise them.  Each call writes the
  *     whole table before reading it, so the previous call's contents do no harm.

@@ -52,6 +52,7 @@ struct GArgs {
     hc_track_opts o;
     hc_step_record *log;
     int log_cap;
+    long long log0;           // corrector stages before this call (the log's offset)
 };
 
 __device__ __forceinline__ bool g_active(const GStage &g)
@@ -310,7 +311,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_end(GArgs a)
     const int n = a.S.n, tid = threadIdx.x;
     if (st.phase == 1) {
         stage_finish<L>(a.o, st, sh, n, a.z, a.zp, a.zpp, a.zh, a.ZP, g.t1, g.h, g.it, g.nst, g.conv, g.res,
-                        g.res_first, g.cond, a.log, a.log_cap);
+                        g.res_first, g.cond, a.log, a.log_cap, a.log0);
     } else if (st.phase == 2) {
         for (int q = tid; q < 2 * L * n; q += HC_TB) a.z[q] = a.zh[q];
         st.end_its += g.it;
@@ -372,8 +373,13 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
 
 using namespace hc;
 
-// One path per call to this function: workspace, graph, replays, statistics.
-int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const hc_track_opts *o,
+void hc_stats_of(const PathState &q, hc_path_stats &r);
+
+// One path per call to this function: workspace, graph, replays, statistics.  With a
+// state (hc_track_resume) the path starts from it, the previous points are the caller's
+// hist (x0 == x1 is the current point), and at most max_stages stages run.
+int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double *hist,
+                       hc_path_state *state, int max_stages, const hc_track_opts *o,
                        hc_path_stats *stats, hc_step_record *log, int log_cap, cudaStream_t st)
 {
     const int n = s->n, L = s->prec;
@@ -413,8 +419,8 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     a.g = (GStage *)(b + o_g);
     a.x0 = x0;
     a.z = x1;
-    a.zp = (double *)(b + o_zp);
-    a.zpp = (double *)(b + o_zpp);
+    a.zp = hist ? hist : (double *)(b + o_zp);
+    a.zpp = hist ? hist + 2 * L * (size_t)n : (double *)(b + o_zpp);
     a.zh = (double *)(b + o_zh);
     a.ZP = (double *)(b + o_ZP);
     a.PW = (double *)(b + o_pw);
@@ -434,6 +440,8 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     a.o = *o;
     a.log = log;
     a.log_cap = log_cap;
+    const long long n0 = state && state->phase != 0 ? state->n_corr : 0;
+    a.log0 = n0;
     cudaStream_t cs = nullptr;
     cudaEvent_t ready = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -441,6 +449,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, off, st);
+    if (e == cudaSuccess && state) e = cudaMemcpyAsync(a.st, state, sizeof(PathState), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_cb, cbeg.data(), sizeof(int32_t) * nchunks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_ce, cend.data(), sizeof(int32_t) * nchunks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_ep, eptr.data(), sizeof(int32_t) * (ne + 1), cudaMemcpyHostToDevice, st);
@@ -454,17 +463,21 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     }
     PathState hs;
     memset(&hs, 0, sizeof hs);
-    // every replay is one corrector stage, or end-game iterations; the path ends within
-    // max_steps stages and end_it / max_it + 1 end-game replays
-    const long long limit = (long long)o->max_steps + o->end_it + 2;
-    for (long long r = 0; !rc && r < limit; r++) {
+    if (state) hs = *state;
+    // every replay is one corrector stage, or end-game iterations; the path ends (or spends
+    // this call's stages) within min(max_steps, max_stages) stages and end_it / max_it + 1
+    // end-game replays
+    const long long cap = o->max_steps < max_stages ? o->max_steps : max_stages;
+    const long long limit = cap + o->end_it + 2;
+    bool spent = hs.phase == 3;
+    for (long long r = 0; !rc && !spent && r < limit; r++) {
         e = cudaGraphLaunch(exec, cs);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, a.st, sizeof hs, cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
         if (e != cudaSuccess) rc = hc_cuda_fail(e, "stage graph replay");
-        if (hs.phase == 3) break;
+        spent = hs.phase == 3 || (hs.phase == 1 && hs.n_corr - n0 >= max_stages);
     }
-    if (!rc && hs.phase != 3) rc = hc_fail(HC_ETIMEOUT, "large path unfinished after the replay limit");
+    if (!rc && !spent) rc = hc_fail(HC_ETIMEOUT, "large path unfinished after the replay limit");
     if (exec) cudaGraphExecDestroy(exec);
     if (ready) {
         cudaEventRecord(ready, cs);
@@ -477,14 +490,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const h
     }
     cudaFree(ws);
     if (rc) return rc;
-    stats->n_succ = hs.n_succ;
-    stats->n_corr = hs.n_corr;
-    stats->newton_its = hs.nits;
-    stats->min_step = hs.n_succ ? hs.minstep : 0.0;
-    stats->avg_step = hs.n_succ ? hs.sumstep / (double)hs.n_succ : 0.0;
-    stats->t_end = hs.t;
-    stats->res_end = hs.res_end;
-    stats->status = hs.status;
-    stats->end_its = hs.end_its;
+    hc_stats_of(hs, *stats);
+    if (state) *state = hs;
     return HC_SUCCESS;
 }

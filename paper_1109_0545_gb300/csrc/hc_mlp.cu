@@ -182,8 +182,11 @@ static size_t grad_smem()
 
 using namespace hc;
 
-static float *g_mlp_partial = nullptr;
-static size_t g_mlp_partial_bytes = 0;
+// per-device workspace of the partial gradients (grown on demand) and the kernel's
+// shared-memory attribute, each keyed by the device that is current at the call
+#define HC_MLP_MAX_DEVICES 64
+static float *g_mlp_partial[HC_MLP_MAX_DEVICES];
+static size_t g_mlp_partial_bytes[HC_MLP_MAX_DEVICES];
 
 extern "C" int hc_mlp_grad(const float *params, int nrec, const float *feat, const float *target,
                            const int32_t *accepted, float kappa, float *grad, float *loss, void *stream)
@@ -191,32 +194,33 @@ extern "C" int hc_mlp_grad(const float *params, int nrec, const float *feat, con
     if (!params || !feat || !target || !accepted || !grad) return hc_fail(HC_EINVAL, "NULL argument");
     if (nrec < 1) return hc_fail(HC_EINVAL, "nrec = %d < 1", nrec);
     if (!(kappa > 0.0f)) return hc_fail(HC_EINVAL, "kappa must be positive");
+    int dev = 0;
+    HC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= HC_MLP_MAX_DEVICES)
+        return hc_fail(HC_EINVAL, "device %d beyond the %d supported", dev, HC_MLP_MAX_DEVICES);
     const int nblk = (nrec + MLP_TILE - 1) / MLP_TILE;
     const size_t need = sizeof(float) * (size_t)nblk * (MLP_NP + 1);
-    if (need > g_mlp_partial_bytes) {
-        if (g_mlp_partial) {
+    if (need > g_mlp_partial_bytes[dev]) {
+        if (g_mlp_partial[dev]) {
             HC_CUDA_TRY(cudaDeviceSynchronize());
-            cudaFree(g_mlp_partial);
-            g_mlp_partial = nullptr;
-            g_mlp_partial_bytes = 0;
+            cudaFree(g_mlp_partial[dev]);
+            g_mlp_partial[dev] = nullptr;
+            g_mlp_partial_bytes[dev] = 0;
         }
-        HC_CUDA_TRY(cudaMalloc(&g_mlp_partial, need));
-        g_mlp_partial_bytes = need;
+        HC_CUDA_TRY(cudaMalloc(&g_mlp_partial[dev], need));
+        g_mlp_partial_bytes[dev] = need;
     }
     cudaStream_t st = (cudaStream_t)stream;
     // the dynamic shared-memory limit is a per-device attribute of the kernel
-    static bool attr[64];
-    int dev = 0;
-    HC_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return hc_fail(HC_EINVAL, "device %d beyond the 64 supported", dev);
+    static bool attr[HC_MLP_MAX_DEVICES];
     if (!attr[dev]) {
         HC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
         attr[dev] = true;
     }
     const float inv_n = 1.0f / (float)nrec;
     k_mlp_grad<<<nblk, MLP_THREADS, grad_smem(), st>>>(params, nrec, feat, target, accepted, kappa, inv_n,
-                                                       g_mlp_partial);
-    k_mlp_reduce<<<(MLP_NP + 1 + 255) / 256, 256, 0, st>>>(g_mlp_partial, nblk, inv_n, grad, loss);
+                                                       g_mlp_partial[dev]);
+    k_mlp_reduce<<<(MLP_NP + 1 + 255) / 256, 256, 0, st>>>(g_mlp_partial[dev], nblk, inv_n, grad, loss);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return hc_cuda_fail(e, "k_mlp_grad launch");
     return HC_SUCCESS;

@@ -27,14 +27,17 @@ struct TrackArgs {
     const long long *xoff;    // [npaths] offset (doubles) of path p in x0/x1
     const double *x0;
     double *x1;
-    double *vecs;             // per path: previous, second previous, predicted+corrected,
-                              // tangent (each 2 L n doubles)
+    double *hist;             // per path at 3 xoff[p]: previous accepted point, second
+                              // previous, tangent (each 2 L n doubles)
+    double *zh;               // per path at xoff[p]: the predicted, then corrected point
     PathState *st;
+    const long long *n0;      // [npaths] corrector stages done before this call (log
+                              // offset and stage budget of the call)
     hc_track_opts o;
     char *slots;
     SlotLayout lay;
     int *queue;
-    int *active;
+    int *active;              // paths that may still advance in this call
     const int *order;         // [npaths] paths in the order they are taken: largest
                               // evaluation cost first, so the last ones to start are short
     hc_step_record *log;
@@ -42,6 +45,7 @@ struct TrackArgs {
     int npaths;
     int nmax;                 // largest n of the batch
     int b_smem;               // the FP64 factors in shared memory (else in the slot)
+    int max_stages;           // corrector stages per path in this call
 };
 
 // Dynamic shared memory of a tracking block, in doubles: Y, RV [2][nmax] each, PIV
@@ -72,7 +76,8 @@ template <int L> __device__ __forceinline__ Slot<L> slot_of(const TrackArgs &a, 
 
 
 //
-// Advance path p by at most max_stages corrector stages (then its end game, once t = 1).
+// Advance path p by at most max_stages corrector stages (then its end game, once t = 1),
+// within the call's budget of a.max_stages stages per path.
 // Every thread keeps the same copy of the path's scalars: each decision is taken from
 // values that block reductions broadcast, so all threads follow the same branch.
 //
@@ -83,13 +88,15 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
     const hc_track_opts &o = a.o;
     const int n = S.n, tid = threadIdx.x;
     double *z = a.x1 + a.xoff[p];
-    double *zp = a.vecs + 4 * a.xoff[p];
+    double *zp = a.hist + 3 * a.xoff[p];
     double *zpp = zp + 2 * L * n;
-    double *zh = zpp + 2 * L * n;
-    double *tv = zh + 2 * L * n;  // [2][n] dx/dt at the last accepted point (tangent predictor)
+    double *tv = zpp + 2 * L * n;  // [2][n] dx/dt at the last accepted point (tangent predictor)
+    double *zh = a.zh + a.xoff[p];
     const bool tangent = o.predictor == HC_PRED_TANGENT;
     PathState st = a.st[p];
-    if (st.phase == 3) return;
+    const long long n0 = a.n0[p];
+    // done, or this call's stages spent (the path was counted out of `active` then)
+    if (st.phase == 3 || (st.phase == 1 && st.n_corr - n0 >= a.max_stages)) return;
     if (st.phase == 0) {
         for (int q = tid; q < 2 * L * n; q += HC_TB) z[q] = a.x0[a.xoff[p] + q];
         path_init(st, o, p);
@@ -97,7 +104,7 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
     }
     hc_step_record *log = a.log ? a.log + (size_t)p * a.log_cap : nullptr;
     int stages = 0;
-    while (st.phase == 1 && stages < max_stages) {
+    while (st.phase == 1 && stages < max_stages && st.n_corr - n0 < a.max_stages) {
         double t1, h;
         stage_predict<L>(o, st, n, z, zp, zpp, tv, zh, w.ZP, t1, h);
         // corrector: Alg. 4.1
@@ -121,7 +128,7 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
         }
         const long long succ0 = st.n_succ;
         stage_finish<L>(o, st, sh, n, z, zp, zpp, zh, w.ZP, t1, h, it, nst, conv, res, res_first, cond,
-                        log, a.log_cap);
+                        log, a.log_cap, n0);
         if (tangent && st.n_succ > succ0) {
             for (int q = tid; q < 2 * n; q += HC_TB) tv[q] = -w.Y[q];
             __syncthreads();
@@ -149,7 +156,7 @@ __device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShare
     __syncthreads();
     if (tid == 0) {
         a.st[p] = st;
-        if (st.phase == 3) atomicSub(a.active, 1);
+        if (st.phase == 3 || st.n_corr - n0 >= a.max_stages) atomicSub(a.active, 1);
     }
     __syncthreads();
 }
@@ -179,7 +186,8 @@ __global__ void __launch_bounds__(HC_TB, L == 4 ? 3 : 4) k_track(TrackArgs a, in
 
 using namespace hc;
 
-int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, const hc_track_opts *o,
+int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double *hist,
+                       hc_path_state *state, int max_stages, const hc_track_opts *o,
                        hc_path_stats *stats, hc_step_record *log, int log_cap, cudaStream_t st);
 
 extern "C" void hc_track_opts_default(hc_track_opts *o)
@@ -261,12 +269,39 @@ struct DevBuf {
     ~DevBuf() { if (p) cudaFree(p); }
 };
 
-extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x1,
-                             const hc_track_opts *opts, hc_path_stats *stats, hc_step_record *log,
-                             int log_cap, void *stream)
+// hc_path_stats of a path state (the statistics of Tables 2-3)
+void hc_stats_of(const PathState &q, hc_path_stats &r)
 {
-    if (!sys || npaths < 1) return hc_fail(HC_EINVAL, "need npaths >= 1 systems");
-    if (!x0 || !x1 || !stats) return hc_fail(HC_EINVAL, "x0, x1 or stats is NULL");
+    r.n_succ = q.n_succ;
+    r.n_corr = q.n_corr;
+    r.newton_its = q.nits;
+    r.min_step = q.n_succ ? q.minstep : 0.0;
+    r.avg_step = q.n_succ ? q.sumstep / (double)q.n_succ : 0.0;
+    r.t_end = q.t;
+    r.res_end = q.res_end;
+    r.status = q.status;
+    r.end_its = q.end_its;
+}
+
+// A state handed to hc_track_resume: a known phase, a history that fits, a step.
+int hc_check_state(const hc_path_state &q, int p)
+{
+    if (q.phase < 0 || q.phase > 3) return hc_fail(HC_EINVAL, "state %d: unknown phase %d", p, q.phase);
+    if (q.phase == 0 || q.phase == 3) return HC_SUCCESS;
+    if (q.nhist < 1 || q.nhist > 3) return hc_fail(HC_EINVAL, "state %d: nhist %d out of [1, 3]", p, q.nhist);
+    if (!(q.lambda > 0.0) || !(q.t >= 0.0 && q.t <= 1.0) || q.n_corr < 0)
+        return hc_fail(HC_EINVAL, "state %d: bad t, lambda or stage count", p);
+    if (q.phase == 2 && q.t < 1.0) return hc_fail(HC_EINVAL, "state %d: end game before t = 1", p);
+    if (q.phase == 1 && q.t >= 1.0) return hc_fail(HC_EINVAL, "state %d: tracking at t = 1", p);
+    return HC_SUCCESS;
+}
+
+// hc_track_path (state == NULL: every path from t = 0, no stage budget) and
+// hc_track_resume (state != NULL: the caller's states, x in place, the caller's hist).
+static int track_impl(hc_system *const *sys, int npaths, const double *x0, double *x1, double *hist_io,
+                      hc_path_state *state_io, int max_stages, const hc_track_opts *opts,
+                      hc_path_stats *stats, hc_step_record *log, int log_cap, void *stream)
+{
     if (log_cap < 0 || (log_cap > 0 && !log)) return hc_fail(HC_EINVAL, "bad log buffer");
     int rc = check_opts(opts);
     if (rc) return rc;
@@ -282,6 +317,7 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         if (s->npoly != s->n) return hc_fail(HC_EINVAL, "system %d: tracking needs npoly == n", p);
         if (s->min_deg < 1) return hc_fail(HC_EINVAL, "system %d: a polynomial of degree 0", p);
         if (s->n > 256) return hc_fail(HC_EINVAL, "system %d: n = %d above the tracker's 256", p, s->n);
+        if (state_io && (rc = hc_check_state(state_io[p], p))) return rc;
         hs[p] = s->dev;
         off[p] = total;
         total += 2LL * L * s->n;
@@ -293,7 +329,9 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     if (opts->mode == HC_TRACK_GRID) {
         // one path at a time, each on the whole GPU
         for (int p = 0; p < npaths; p++) {
-            rc = hc_track_grid_path(sys[p], x0 + off[p], x1 + off[p], opts, &stats[p],
+            hc_path_stats tmp;
+            rc = hc_track_grid_path(sys[p], x0 + off[p], x1 + off[p], hist_io ? hist_io + 3 * off[p] : nullptr,
+                                    state_io ? &state_io[p] : nullptr, max_stages, opts, stats ? &stats[p] : &tmp,
                                     log_cap > 0 ? log + (size_t)p * log_cap : nullptr, log_cap,
                                     (cudaStream_t)stream);
             if (rc) return rc;
@@ -328,26 +366,32 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
 
     size_t b_sys = hc_align256(sizeof(DevSys) * npaths);
     size_t b_off = hc_align256(sizeof(long long) * npaths);
-    size_t b_vec = hc_align256(sizeof(double) * 4 * (size_t)total);
+    size_t b_n0 = hc_align256(sizeof(long long) * npaths);
+    size_t b_hist = hist_io ? 0 : hc_align256(sizeof(double) * 3 * (size_t)total);
+    size_t b_zh = hc_align256(sizeof(double) * (size_t)total);
     size_t b_st = hc_align256(sizeof(PathState) * npaths);
     size_t b_ord = hc_align256(sizeof(int) * npaths);
     size_t b_ctr = 256;
-    size_t bytes = b_sys + b_off + b_vec + b_st + b_ord + b_ctr + lay.stride * (size_t)grid;
+    size_t bytes = b_sys + b_off + b_n0 + b_hist + b_zh + b_st + b_ord + b_ctr + lay.stride * (size_t)grid;
     DevBuf ws;
     HC_CUDA_TRY(cudaMalloc(&ws.p, bytes));
     char *b = (char *)ws.p;
+    auto take = [&](size_t nb) { char *at = b; b += nb; return at; };
     cudaStream_t st = (cudaStream_t)stream;
     TrackArgs a;
-    a.sys = (const DevSys *)b;
-    a.xoff = (const long long *)(b + b_sys);
-    a.vecs = (double *)(b + b_sys + b_off);
-    a.st = (PathState *)(b + b_sys + b_off + b_vec);
-    int *ord = (int *)(b + b_sys + b_off + b_vec + b_st);
-    int *ctr = (int *)(b + b_sys + b_off + b_vec + b_st + b_ord);
+    a.sys = (const DevSys *)take(b_sys);
+    a.xoff = (const long long *)take(b_off);
+    long long *n0 = (long long *)take(b_n0);
+    a.n0 = n0;
+    a.hist = hist_io ? hist_io : (double *)take(b_hist);
+    a.zh = (double *)take(b_zh);
+    a.st = (PathState *)take(b_st);
+    int *ord = (int *)take(b_ord);
+    int *ctr = (int *)take(b_ctr);
     a.queue = ctr;
     a.active = ctr + 1;
     a.order = ord;
-    a.slots = b + b_sys + b_off + b_vec + b_st + b_ord + b_ctr;
+    a.slots = b;
     a.lay = lay;
     a.x0 = x0;
     a.x1 = x1;
@@ -357,9 +401,22 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     a.npaths = npaths;
     a.nmax = nmax;
     a.b_smem = b_smem;
+    a.max_stages = max_stages;
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.sys, hs.data(), sizeof(DevSys) * npaths, cudaMemcpyHostToDevice, st));
     HC_CUDA_TRY(cudaMemcpyAsync((void *)a.xoff, off.data(), sizeof(long long) * npaths, cudaMemcpyHostToDevice, st));
-    HC_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(PathState) * npaths, st));
+    std::vector<long long> hn0((size_t)npaths, 0);
+    int h_active = npaths;
+    if (state_io) {
+        h_active = 0;
+        for (int p = 0; p < npaths; p++) {
+            hn0[p] = state_io[p].phase == 0 ? 0 : state_io[p].n_corr;
+            h_active += state_io[p].phase != 3;
+        }
+        HC_CUDA_TRY(cudaMemcpyAsync(a.st, state_io, sizeof(PathState) * npaths, cudaMemcpyHostToDevice, st));
+    } else {
+        HC_CUDA_TRY(cudaMemsetAsync(a.st, 0, sizeof(PathState) * npaths, st));
+    }
+    HC_CUDA_TRY(cudaMemcpyAsync(n0, hn0.data(), sizeof(long long) * npaths, cudaMemcpyHostToDevice, st));
     // largest first by the cost of a stage (FP64 instructions of one evaluation plus the LU;
     // the number of stages is not known in advance), so the last paths to start are short.
     // The first wave (one path per resident block) is then shuffled: the block scheduler
@@ -388,7 +445,7 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         }
     }
     HC_CUDA_TRY(cudaMemcpyAsync(ord, horder.data(), sizeof(int) * npaths, cudaMemcpyHostToDevice, st));
-    int hctr[2] = {0, npaths};
+    int hctr[2] = {0, h_active};
     HC_CUDA_TRY(cudaMemcpyAsync(ctr, hctr, sizeof hctr, cudaMemcpyHostToDevice, st));
 
     if (opts->mode == HC_TRACK_PERSISTENT) {
@@ -397,7 +454,7 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
         else launch_track<4>(a, grid, 1, smem, st);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return hc_cuda_fail(e, "k_track launch");
-    } else {
+    } else if (h_active > 0) {
         // one predictor-corrector stage per launch, graph_steps launches per graph
         cudaStream_t cs;
         HC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -417,10 +474,11 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
             e = cudaStreamEndCapture(cs, &graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-        int h_active = npaths;
-        // every stage either accepts, halves the step or ends the path, so a path ends
-        // within max_steps stages (plus its end game, taken in the same launch)
-        const long long max_replays = (long long)opts->max_steps / opts->graph_steps + 2;
+        // every stage either accepts, halves the step or ends the path, so a path ends (or
+        // spends this call's stages) within min(max_steps, max_stages) stages, plus its
+        // end game, taken in the same launch
+        const long long cap = opts->max_steps < max_stages ? opts->max_steps : max_stages;
+        const long long max_replays = cap / opts->graph_steps + 2;
         for (long long r = 0; e == cudaSuccess && r < max_replays && h_active > 0; r++) {
             e = cudaGraphLaunch(exec, cs);
             if (e == cudaSuccess) e = cudaMemcpyAsync(&h_active, a.active, sizeof(int), cudaMemcpyDeviceToHost, cs);
@@ -439,17 +497,27 @@ extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0
     HC_CUDA_TRY(cudaMemcpyAsync(hst.data(), a.st, sizeof(PathState) * npaths, cudaMemcpyDeviceToHost, st));
     HC_CUDA_TRY(cudaStreamSynchronize(st));
     for (int p = 0; p < npaths; p++) {
-        const PathState &q = hst[p];
-        hc_path_stats &r = stats[p];
-        r.n_succ = q.n_succ;
-        r.n_corr = q.n_corr;
-        r.newton_its = q.nits;
-        r.min_step = q.n_succ ? q.minstep : 0.0;
-        r.avg_step = q.n_succ ? q.sumstep / (double)q.n_succ : 0.0;
-        r.t_end = q.t;
-        r.res_end = q.res_end;
-        r.status = q.status;
-        r.end_its = q.end_its;
+        if (stats) hc_stats_of(hst[p], stats[p]);
+        if (state_io) state_io[p] = hst[p];
     }
     return HC_SUCCESS;
+}
+
+extern "C" int hc_track_path(hc_system *const *sys, int npaths, const double *x0, double *x1,
+                             const hc_track_opts *opts, hc_path_stats *stats, hc_step_record *log,
+                             int log_cap, void *stream)
+{
+    if (!sys || npaths < 1) return hc_fail(HC_EINVAL, "need npaths >= 1 systems");
+    if (!x0 || !x1 || !stats) return hc_fail(HC_EINVAL, "x0, x1 or stats is NULL");
+    return track_impl(sys, npaths, x0, x1, nullptr, nullptr, 0x7fffffff, opts, stats, log, log_cap, stream);
+}
+
+extern "C" int hc_track_resume(hc_system *const *sys, int npaths, double *x, double *hist,
+                               hc_path_state *state, int max_stages, const hc_track_opts *opts,
+                               hc_path_stats *stats, hc_step_record *log, int log_cap, void *stream)
+{
+    if (!sys || npaths < 1) return hc_fail(HC_EINVAL, "need npaths >= 1 systems");
+    if (!x || !hist || !state) return hc_fail(HC_EINVAL, "x, hist or state is NULL");
+    if (max_stages < 1) return hc_fail(HC_EINVAL, "max_stages = %d < 1", max_stages);
+    return track_impl(sys, npaths, x, x, hist, state, max_stages, opts, stats, log, log_cap, stream);
 }

@@ -8,17 +8,9 @@
 
 namespace hc {
 
-struct PathState {
-    double t, tp, tpp, lambda, minstep, sumstep, res_end, pad;
-    long long n_succ, n_corr, nits;
-    int nhist, consec, status, phase;  // phase: 0 new, 1 tracking, 2 end game, 3 done
-    int end_its, pad2;
-    // the last three corrector stages (index 0 = latest), for the step proposer
-    double hl[3], hr[3], pcd, cond;
-    int hi[3], pad3;
-    double lam_plain;  // the plain controller's step, run alongside the proposer
-    long long pid;     // path index (the exploration generator's stream)
-};
+// The path's scalars between corrector stages: the public hc_path_state (include/hc.h),
+// which hc_track_resume saves and restarts from.
+typedef hc_path_state PathState;
 
 // SplitMix64 (Steele, Lea & Flood 2014): one output of the generator at counter x
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
@@ -142,7 +134,7 @@ template <int L>
 __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared &sh, int n, double *z,
                              double *zp, double *zpp, const double *zh, const double *ZP, double t1, double h,
                              int it, int nst, int conv, double res, double res_first, double cond,
-                             hc_step_record *log, int log_cap)
+                             hc_step_record *log, int log_cap, long long log0)
 {
     const int tid = threadIdx.x;
         st.nits += it;
@@ -162,8 +154,9 @@ __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared 
                 m = fmax(m, sqrt(c_abs2_lead(c_sub(ld_c<L>(zh, n, j), ld_c<L>(ZP, n, j)))));
             pcd = block_max(m, sh);
         }
-        if (log && tid == 0 && st.n_corr <= log_cap) {
-            hc_step_record &r = log[st.n_corr - 1];
+        // the log holds the stages of this call: stage n_corr is record n_corr - 1 - log0
+        if (log && tid == 0 && st.n_corr - log0 <= log_cap) {
+            hc_step_record &r = log[st.n_corr - 1 - log0];
             r.t = st.t;
             r.lambda = h;
             r.res_first = res_first;

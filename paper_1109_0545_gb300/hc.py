@@ -49,6 +49,19 @@ class PathStats(ct.Structure):
                 ("res_end", ct.c_double), ("status", ct.c_int32), ("end_its", ct.c_int32)]
 
 
+class PathState(ct.Structure):
+    """hc_path_state (include/hc.h): a path's state between calls of hc_track_resume."""
+    _fields_ = [("t", ct.c_double), ("tp", ct.c_double), ("tpp", ct.c_double),
+                ("lambda_", ct.c_double), ("minstep", ct.c_double), ("sumstep", ct.c_double),
+                ("res_end", ct.c_double), ("pad", ct.c_double), ("n_succ", ct.c_int64),
+                ("n_corr", ct.c_int64), ("nits", ct.c_int64), ("nhist", ct.c_int32),
+                ("consec", ct.c_int32), ("status", ct.c_int32), ("phase", ct.c_int32),
+                ("end_its", ct.c_int32), ("pad2", ct.c_int32), ("hl", ct.c_double * 3),
+                ("hr", ct.c_double * 3), ("pcd", ct.c_double), ("cond", ct.c_double),
+                ("hi", ct.c_int32 * 3), ("pad3", ct.c_int32), ("lam_plain", ct.c_double),
+                ("pid", ct.c_int64)]
+
+
 STEP_RECORD_DTYPE = np.dtype([("t", "f8"), ("lam", "f8"), ("res_first", "f8"), ("res_last", "f8"),
                               ("pc_dist", "f8"), ("cond_log10", "f8"), ("iters", "i4"),
                               ("accepted", "i4")])
@@ -103,6 +116,9 @@ def load(build_if_missing: bool = True):
         L.hc_track_path.argtypes = [ct.POINTER(vp), i, vp, vp, ct.POINTER(TrackOpts),
                                     ct.POINTER(PathStats), vp, i, vp]
         L.hc_track_path.restype = i
+        L.hc_track_resume.argtypes = [ct.POINTER(vp), i, vp, vp, ct.POINTER(PathState), i,
+                                      ct.POINTER(TrackOpts), ct.POINTER(PathStats), vp, i, vp]
+        L.hc_track_resume.restype = i
         f = ct.c_float
         L.hc_mlp_grad.argtypes = [vp, i, vp, vp, vp, f, vp, vp, vp]
         L.hc_mlp_grad.restype = i
@@ -253,6 +269,46 @@ def hc_track_path(systems, x0, x1, opts: TrackOpts, log=None, log_cap: int = 0,
                                                  _stream(stream)))
     keys = [f[0] for f in PathStats._fields_]
     return [{k: getattr(st, k) for k in keys} for st in stats]
+
+
+def new_states(npaths: int):
+    """npaths zeroed hc_path_state records: phase 0, start at t = 0 from x."""
+    return (PathState * npaths)()
+
+
+def hc_track_resume(systems, x, hist, states, max_stages: int, opts: TrackOpts, log=None,
+                    log_cap: int = 0, stream=None) -> list[dict]:
+    """Advance each path by at most max_stages corrector stages from its state (updated
+    in place, a ctypes array of PathState from new_states); x, hist: device buffers in
+    the packings of hc_track_resume (x as pack_paths, hist 3 vectors per path)."""
+    handles = (ct.c_void_p * len(systems))(*[s.handle for s in systems])
+    stats = (PathStats * len(systems))()
+    _check("hc_track_resume", load().hc_track_resume(handles, len(systems), _ptr(x), _ptr(hist), states,
+                                                     int(max_stages), ct.byref(opts), stats, _ptr(log),
+                                                     int(log_cap), _stream(stream)))
+    keys = [f[0] for f in PathStats._fields_]
+    return [{k: getattr(st, k) for k in keys} for st in stats]
+
+
+def pack_hist(prev: list[np.ndarray], prev2: list[np.ndarray], L: int) -> np.ndarray:
+    """The hist packing of hc_track_resume from per-path previous points (limbs [n][2][L]
+    each); the tangent slot is zero."""
+    out = []
+    for a, b in zip(prev, prev2):
+        n = a.shape[0]
+        out += [pack_paths([a]), pack_paths([b]), np.zeros(2 * L * n)]
+    return np.concatenate(out)
+
+
+def unpack_hist(buf: np.ndarray, dims: list[int], L: int):
+    """Inverse of pack_hist: lists of previous and second previous points (limbs)."""
+    prev, prev2, o = [], [], 0
+    for n in dims:
+        w = 2 * L * n
+        prev += unpack_paths(buf[o:o + w], [n], L)
+        prev2 += unpack_paths(buf[o + w:o + 2 * w], [n], L)
+        o += 3 * w
+    return prev, prev2
 
 
 def pack_paths(points: list[np.ndarray]) -> np.ndarray:

@@ -111,7 +111,38 @@ def test_null_handle_calls_fail_cleanly():
     opts = hc.hc_track_opts_default()
     stats = (hc.PathStats * 1)()
     assert lib.hc_track_path(None, 1, None, None, ct.byref(opts), stats, None, 0, None) == hc.HC_EINVAL
+    states = hc.new_states(1)
+    assert lib.hc_track_resume(None, 1, None, None, states, 1, ct.byref(opts), stats, None, 0, None) == hc.HC_EINVAL
     assert lib.hc_last_error()  # a message says why
+
+
+@pytest.mark.gpu
+def test_resume_rejects_bad_states_before_any_launch(small):
+    """hc_track_resume checks its arguments and every saved state on the host: a NULL
+    buffer, max_stages < 1, an unknown phase, a history of 0 or 4 points, an end game
+    before t = 1, tracking at t = 1.  Every case returns HC_EINVAL without a device."""
+    s = synth.regular_system(np.random.default_rng(6), 3, 4, (1, 2), (1, 2), lead=3)
+    h = hc.system_from(s, 2, 0.6 + 0.8j)   # loading a system needs the device
+    lib = hc.load()
+    opts = hc.hc_track_opts_default()
+    stats = (hc.PathStats * 1)()
+    handles = (ct.c_void_p * 1)(h.handle)
+    fake = ct.c_void_p(256)   # never dereferenced: the checks come first
+
+    def call(state, max_stages=1, x=fake, hist=fake):
+        return lib.hc_track_resume(handles, 1, x, hist, state, max_stages, ct.byref(opts), stats, None, 0, None)
+
+    st = hc.new_states(1)
+    assert call(st, x=None) == hc.HC_EINVAL
+    assert call(st, hist=None) == hc.HC_EINVAL
+    assert call(st, max_stages=0) == hc.HC_EINVAL
+    for field, value, phase, t in (("phase", 7, 7, 0.5), ("nhist", 0, 1, 0.5), ("nhist", 4, 1, 0.5),
+                                   ("t", 0.5, 2, 0.5), ("t", 1.0, 1, 1.0)):
+        st = hc.new_states(1)
+        st[0].phase, st[0].nhist, st[0].lambda_, st[0].t = phase, 2, 0.01, t
+        setattr(st[0], field, value)
+        assert call(st) == hc.HC_EINVAL, (field, value)
+    h.free()
 
 
 def test_option_defaults_follow_the_readings():
@@ -141,12 +172,13 @@ def test_struct_layouts_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    mirrors = {"hc_track_opts": hc.TrackOpts, "hc_path_stats": hc.PathStats}
+    mirrors = {"hc_track_opts": hc.TrackOpts, "hc_path_stats": hc.PathStats, "hc_path_state": hc.PathState}
+    cnames = {"lambda_": "lambda"}   # a Python keyword in the ctypes mirror
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hc.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
-            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {cnames.get(fname, fname)}));')
     lines.append('printf("hc_step_record size %zu\\n", sizeof(hc_step_record));')
     for fname, cfield in (("t", "t"), ("lam", "lambda"), ("res_first", "res_first"), ("res_last", "res_last"),
                           ("pc_dist", "pc_dist"), ("cond_log10", "cond_log10"), ("iters", "iters"),
