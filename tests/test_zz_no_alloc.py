@@ -32,7 +32,7 @@ def _run(torch, fn, sysh, s, L, pts, t):
     return hc.from_soa(f.cpu().numpy()), hc.from_soa(J.cpu().numpy())
 
 
-@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("L", [1, 2, 4])
 def test_noalloc_matches_eval_jac_on_two_calls_in_a_row(L):
     torch = _torch()
     s, pts, gamma = synth.eval_throughput(2, npts=3000)
@@ -45,6 +45,39 @@ def test_noalloc_matches_eval_jac_on_two_calls_in_a_row(L):
         ref_f, ref_J = _run(torch, hc.hc_eval_jac, sysh, s, L, p, t)
         assert np.all(rel_err_per_point(got_f, ref_f) <= TOL[L])
         assert np.all(rel_err_per_point(got_J, ref_J) <= TOL[L])
+    sysh.free()
+
+
+def test_noalloc_shared_monomial_scheme_on_two_calls_in_a_row():
+    """The shared-monomial scheme (a common support: Table 1's 40 x 40 system with 200
+    monomials of degree up to 80, whose power table takes about 100 KB per DD point)."""
+    torch = _torch()
+    s, gamma = synth.common_support_system(1)
+    sysh = hc.system_from(s, 2, gamma)
+    sysh.set_eval_mode(hc.HC_EVAL_SHARED)
+    rng = np.random.default_rng(78)
+    for npts, t in ((300, 0.7), (57, -1.0)):
+        p = synth.torus_points(rng, npts, s.n)
+        got_f, got_J = _run(torch, hc.hc_eval_jac_noalloc, sysh, s, 2, p, t)
+        ref_f, ref_J = _run(torch, hc.hc_eval_jac, sysh, s, 2, p, t)
+        assert np.all(rel_err_per_point(got_f, ref_f) <= TOL[2])
+        assert np.all(rel_err_per_point(got_J, ref_J) <= TOL[2])
+    sysh.free()
+
+
+def test_noalloc_without_a_power_table():
+    """Exponents at most 2 need no workspace at all: any number of points is accepted."""
+    torch = _torch()
+    rng = np.random.default_rng(79)
+    s = synth.random_system(rng, 6, 10, (1, 4), (1, 2), const_term=True)
+    gamma = synth.unit_complex(rng)
+    sysh = hc.system_from(s, 2, gamma)
+    for npts, t in ((70000, 0.2), (33, 0.9)):
+        p = synth.torus_points(rng, npts, s.n)
+        got_f, got_J = _run(torch, hc.hc_eval_jac_noalloc, sysh, s, 2, p, t)
+        ref_f, ref_J = _run(torch, hc.hc_eval_jac, sysh, s, 2, p, t)
+        assert np.all(rel_err_per_point(got_f, ref_f) <= TOL[2])
+        assert np.all(rel_err_per_point(got_J, ref_J) <= TOL[2])
     sysh.free()
 
 
