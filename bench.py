@@ -33,6 +33,15 @@ WORKLOAD = ("Newton step (eval+Jacobian+homotopy, FP64 LU + DD refinement, updat
             "65,536 unit-torus points, complex double-double, seed 2")
 T_HOM = 0.5
 MAX_REFINE = 6
+L2_NOTE = ("GPU arm: a 256 MiB buffer written between timed steps (L2 is 129 MB); "
+           "host arm: a fresh sample of points every step")
+
+
+def workload_config(npts: int, s, world: int) -> dict:
+    """The config of the JSON line, the same for the GPU arm and the reference arm."""
+    return {"workload": WORKLOAD, "npts": npts, "n": s.n, "monomials": s.nmon,
+            "precision": "complex double-double", "lu": "FP64 LU + DD refinement",
+            "max_refine": MAX_REFINE, "t": T_HOM, "parallelism": f"dp{world}", "l2": L2_NOTE}
 
 
 def parse():
@@ -154,9 +163,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot_t / max(len(steps), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "npts": args.npts, "n": s.n, "monomials": s.nmon,
-                   "precision": "complex double-double", "lu": "FP64 LU + DD refinement",
-                   "max_refine": MAX_REFINE, "t": T_HOM, "parallelism": "host threads"},
+        "config": workload_config(args.npts, s, args.gpus),
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
                          "sample": f"{steps[0][0] if steps else 0} points per step "
                                    f"(about {budget:.0f} s of oracle work), all host cores"},
@@ -192,7 +199,7 @@ def captured_traffic(npts: int):
 PROPOSER = os.path.join(ROOT, "paper_1109_0545_gb300", "data", "proposer_weights.npy")
 
 
-def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=2432, cap=200, plain_sample=2,
+def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=2432, cap=200, plain_sample=16,
                   full_uneven=False):
     """Path steps/s and paths/s of the batched tracker (all paths in one persistent
     kernel, FP64 LU + DD refinement; secant, quadratic, tangent, and quadratic + learned step
@@ -258,7 +265,10 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
                                              "paths_per_s": plain_sample / p_dt,
                                              "sample_paths": plain_sample},
                "batched_all_dd_secant": {"path_steps_per_s": ref_steps / ref_dt,
-                                         "paths_per_s": npaths / ref_dt}}
+                                         "paths_per_s": npaths / ref_dt,
+                                         "ok_paths": sum(1 for x in ref_st if x["status"] == hc.HC_OK),
+                                         "status_hist": np.bincount([x["status"] for x in ref_st],
+                                                                    minlength=7).tolist()}}
         for vname, kw in variants:
             st, ends, dt = run(handles, systems, hc.hc_track_opts_default(**kw, **extra))
             steps = sum(x["n_corr"] for x in st)
@@ -269,6 +279,8 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
             res[vname] = {"path_steps_per_s": steps / dt, "paths_per_s": npaths / dt,
                           "fp64_gops_at_least": gops,
                           "fp64_frac_of_measured_peak_at_least": gops / peak_gops if peak_gops else None,
+                          "speedup_steps_vs_batched_all_dd": (steps / dt) / (ref_steps / ref_dt),
+                          "speedup_paths_vs_batched_all_dd": (npaths / dt) / (npaths / ref_dt),
                           "speedup_steps_vs_plain": (steps / dt) / (p_steps / p_dt),
                           "speedup_paths_vs_plain": (npaths / dt) / (plain_sample / p_dt),
                           "mean_stages": steps / npaths,
@@ -296,6 +308,30 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
                                 "speedup_steps_vs_plain":
                                     (steps / dt) / out["uneven"]["plain_one_path_per_launch"]["path_steps_per_s"]}
     return out
+
+
+def large_path_bench(torch, hc, synth):
+    """The large single path (n = 96, 96 x 1024 monomials, k = 12, exponents 1..5, complex
+    QD, FP64 LU with QD refinement, seed 4) tracked on the whole GPU from t = 0 until it
+    stops: corrector stages, seconds, stages per second, status and the t reached.  (Its
+    stages are compared with the QD oracle in tests/test_gpu_grid.py.)"""
+    import numpy as np
+    s, g = synth.large_path_qd(4)
+    h = hc.system_from(s, 4, g)
+    x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 4)])).cuda()
+    x1 = torch.zeros_like(x0)
+    o = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, mode=hc.HC_TRACK_GRID,
+                                 eps=1e-58, eps_end=1e-58, eps_end_x=1e-58)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = hc.hc_track_path([h], x0, x1, o)[0]
+    dt = time.perf_counter() - t0
+    z = hc.unpack_paths(x1.cpu().numpy(), [s.n], 4)[0]
+    h.free()
+    return {"n": s.n, "monomials": s.nmon, "status": hc.STATUS_NAMES[st["status"]],
+            "stages": int(st["n_corr"]), "accepted": int(st["n_succ"]), "newton_its": int(st["newton_its"]),
+            "t_end": st["t_end"], "min_step": st["min_step"], "seconds": dt, "stages_per_s": st["n_corr"] / dt,
+            "max_abs_z_end": float(np.abs(z[:, 0, 0] + 1j * z[:, 1, 0]).max())}
 
 
 def single_path_bench(torch, hc, synth):
@@ -540,6 +576,57 @@ def mlp_bench(torch, hc, steps=200, batch=8192, nrec=65536):
             "forward_records_per_s": nrec / (ms_fwd * 1e-3)}
 
 
+def compact_extras(ex: dict) -> dict:
+    """The secondary figures in a few hundred bytes (the full record is printed on the line
+    before the main one)."""
+    def r(v, d=3):
+        return None if v is None else float(f"{v:.{d}g}")
+
+    out = {}
+    tr = ex.get("tracker", {})
+    for fam, res in tr.items():
+        if not isinstance(res, dict) or "batched_all_dd_secant" not in res:
+            continue
+        key = "paths_per_s" if fam == "uneven_regular" else "path_steps_per_s"
+        row = {"unit": key, "paths": res["paths"], "cap": res.get("stage_cap"),
+               "plain_1_per_launch": r(res["plain_one_path_per_launch"][key]),
+               "plain_sample_paths": res["plain_one_path_per_launch"]["sample_paths"],
+               "batched_all_dd": r(res["batched_all_dd_secant"][key])}
+        for v in ("batched_secant", "batched_quadratic", "batched_tangent", "batched_quadratic_proposer"):
+            if v in res:
+                row[v.replace("batched_", "mixed_")] = r(res[v][key])
+        if "batched_secant" in res:
+            row["mixed_vs_all_dd_equal_batching"] = r(res["batched_secant"][key] / res["batched_all_dd_secant"][key])
+            row["ok_paths_mixed"] = res["batched_secant"]["ok_paths"]
+            row["same_end_points_1e-28"] = res["batched_secant"]["same_end_point_as_batched_all_dd_1e-28"]
+        out[f"tracker_{fam}"] = row
+    if "uneven_8192_paths" in tr:
+        out["tracker_uneven_8192"] = {"path_steps_per_s": r(tr["uneven_8192_paths"]["path_steps_per_s"])}
+    lp = ex.get("large_path_qd_n96")
+    if lp:
+        out["large_path_qd_n96"] = {k: (r(v, 6) if isinstance(v, float) else v) for k, v in lp.items()
+                                    if k in ("status", "stages", "seconds", "stages_per_s", "t_end")}
+    sp = ex.get("single_path_n8")
+    if sp:
+        out["single_path_n8_stages_per_s"] = {k: r(v["path_steps_per_s"]) for k, v in sp.items() if isinstance(v, dict)}
+    pt = ex.get("paper_tables", {})
+    for k in ("table4_dim40_deg2_qd", "table4_dim40_deg20_qd"):
+        if k in pt:
+            out[k + "_s"] = {"one_block": r(pt[k]["one_block"]["seconds"]), "whole_gpu": r(pt[k]["whole_gpu"]["seconds"]),
+                             "paper_8_cores": pt[k]["paper_8_cores_s"]}
+    cs = ex.get("common_support_table1")
+    if cs:
+        out["table1_eval_points_per_s"] = {"per_term": r(cs["per_term"]["eval_points_per_s"]),
+                                           "shared": r(cs["shared"]["eval_points_per_s"])}
+    q = ex.get("quality_up")
+    if q:
+        out["quality_up_8_gpus"] = r(q.get("quality_up_8_gpus"))
+    for k in ("eval_jac_points_per_s", "eval_jac_qd_points_per_s", "newton_native_dd_lu_points_per_s"):
+        if k in ex:
+            out[k] = r(ex[k])
+    return out
+
+
 def rank_points(rank: int, npts: int, n: int, default):
     """The points rank `rank` evaluates: rank 0 the workload's own, every other rank its
     own seeded draw of the same size (independent problems: weak scaling)."""
@@ -728,6 +815,7 @@ def run_gpu(args):
             del xl, rl, sl, wl
         del xq
         extras = {"tracker": tracker_bench(torch, hc, synth, peak_gops, full_uneven=args.full_uneven),
+                  "large_path_qd_n96": large_path_bench(torch, hc, synth),
                   "single_path_n8": single_path_bench(torch, hc, synth),
                   "paper_tables": paper_tables_bench(torch, hc, synth),
                   "common_support_table1": common_support_bench(torch, hc, synth, peak_gops),
@@ -775,15 +863,15 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "npts": npts, "n": s.n, "monomials": s.nmon,
-                       "precision": "complex double-double", "lu": "FP64 LU + DD refinement",
-                       "max_refine": MAX_REFINE, "t": T_HOM, "parallelism": f"dp{world}",
-                       "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)",
-                       "eval_tiles": tiles},
+            "config": workload_config(npts, s, world),
+            "eval_tiles": tiles,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clk, "wall_s": t_wall,
-            "extras": extras,
+            "extras": compact_extras(extras),
         }
+        if extras:
+            # the full record of the secondary measurements, before the main line
+            print(json.dumps({"bench_detail": extras}), flush=True)
         print(json.dumps(line), flush=True)
     sysh.free()
     if dist:

@@ -48,3 +48,32 @@ def test_binding_fails_loudly_without_the_library():
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert r.returncode != 0
     assert "libhc.so not built" in r.stderr
+
+
+def test_compact_summary_is_small_and_keeps_the_comparisons():
+    """The main JSON line carries a compact summary of the secondary measurements (the
+    driver keeps only the end of the output): under 2.5 KB, with the equal-batching
+    ratio of the mixed-precision tracker against the all-DD one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fam = {"paths": 2432, "stage_cap": 200,
+           "plain_one_path_per_launch": {"path_steps_per_s": 87.0, "paths_per_s": 0.4, "sample_paths": 16},
+           "batched_all_dd_secant": {"path_steps_per_s": 34488.0, "paths_per_s": 170.0, "ok_paths": 0}}
+    for v in ("batched_secant", "batched_quadratic", "batched_tangent", "batched_quadratic_proposer"):
+        fam[v] = {"path_steps_per_s": 55539.0, "paths_per_s": 270.0, "ok_paths": 0,
+                  "same_end_point_as_batched_all_dd_1e-28": 0, "status_hist": [0] * 7}
+    reg = {k: (dict(v) if isinstance(v, dict) else v) for k, v in fam.items()}
+    ex = {"tracker": {"uneven": fam, "uneven_regular": reg},
+          "large_path_qd_n96": {"status": "MIN_STEP", "stages": 1937, "seconds": 30.9, "stages_per_s": 62.7,
+                                "t_end": 0.99999986, "n": 96},
+          "single_path_n8": {"n": 8, "monomials": 104, "plain_all_dd_secant": {"path_steps_per_s": 2254.0},
+                             "fp64_refine_quadratic": {"path_steps_per_s": 3562.0}},
+          "paper_tables": {"table4_dim40_deg2_qd": {"one_block": {"seconds": 1.3}, "whole_gpu": {"seconds": 0.5},
+                                                    "paper_8_cores_s": 62.257}},
+          "common_support_table1": {"per_term": {"eval_points_per_s": 42595.0}, "shared": {"eval_points_per_s": 61020.0}},
+          "quality_up": {"quality_up_8_gpus": 1.85}, "eval_jac_points_per_s": 201926.0}
+    c = bench.compact_extras(ex)
+    assert len(json.dumps(c)) < 2500
+    assert abs(c["tracker_uneven"]["mixed_vs_all_dd_equal_batching"] - 55539.0 / 34488.0) < 1e-2
+    assert c["tracker_uneven"]["plain_sample_paths"] == 16
+    assert c["large_path_qd_n96"]["stages"] == 1937
