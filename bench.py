@@ -246,10 +246,22 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
         variants.append(("batched_quadratic_proposer",
                          dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC,
                               proposer=prop.data_ptr())))
+    from paper_1109_0545_gb300 import autotune
+    # the shape of each family's runs, tuned on the family itself: the uneven family on all
+    # its paths capped at 40 stages (its rate per stage does not depend on the cap); the
+    # regular variant, one wave of paths run to their ends whose makespan is set by the
+    # longest, on the whole run with three shapes
+    tune = {"uneven": (dict(max_steps=40), [(t, b, 0) for t in (64, 128, 256) for b in (0, 2, 3)]),
+            "uneven_regular": (dict(predictor=hc.HC_PRED_QUADRATIC), [(128, 0, 0), (256, 0, 0), (256, 1, 0)])}
     out = {}
     for name, (fam, extra) in fams.items():
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]
         handles = [hc.system_from(sy, 2, g) for sy, g in fam]
+        topts, cands = tune[name]
+        x0t = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(sy.n), 2) for sy in systems])).cuda()
+        tiles = autotune.tune_track(handles, x0t, hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, **topts),
+                                    use_cache=False, candidates=cands)
+        del x0t
         npaths = len(systems)
         it_ops = [opcount.newton_iteration_ops(sy, 2) for sy in systems]
         plain = hc.hc_track_opts_default(lu_mode=hc.HC_LU_NATIVE, **extra)
@@ -261,6 +273,8 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
         ref_st, ref_ends, ref_dt = run(handles, systems, plain)
         ref_steps = sum(x["n_corr"] for x in ref_st)
         res = {"paths": npaths, "stage_cap": extra.get("max_steps"),
+               "tiles": {k: tiles[k] for k in ("threads_per_block", "blocks_per_sm", "factors")},
+               "tile_candidates": tiles["tried"],
                "plain_one_path_per_launch": {"path_steps_per_s": p_steps / p_dt,
                                              "paths_per_s": plain_sample / p_dt,
                                              "sample_paths": plain_sample},
@@ -289,6 +303,7 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
                           "status_hist": np.bincount([x["status"] for x in st], minlength=7).tolist()}
         for h in handles:
             h.free()
+        hc.hc_set_track_tiles(0, 0, 0, 0)
         out[name] = res
     if not full_uneven:
         return out
@@ -316,19 +331,25 @@ def large_path_bench(torch, hc, synth):
     stops: corrector stages, seconds, stages per second, status and the t reached.  (Its
     stages are compared with the QD oracle in tests/test_gpu_grid.py.)"""
     import numpy as np
+    from paper_1109_0545_gb300 import autotune
     s, g = synth.large_path_qd(4)
     h = hc.system_from(s, 4, g)
     x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 4)])).cuda()
     x1 = torch.zeros_like(x0)
     o = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, mode=hc.HC_TRACK_GRID,
                                  eps=1e-58, eps_end=1e-58, eps_end_x=1e-58)
+    # the chunk length of the entry sums, tuned on 8 stages of this path
+    o8 = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, mode=hc.HC_TRACK_GRID, max_steps=8,
+                                  eps=1e-58, eps_end=1e-58, eps_end_x=1e-58)
+    chunk = autotune.tune_grid_chunk(h, x0, o8, use_cache=False)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = hc.hc_track_path([h], x0, x1, o)[0]
     dt = time.perf_counter() - t0
     z = hc.unpack_paths(x1.cpu().numpy(), [s.n], 4)[0]
     h.free()
-    return {"n": s.n, "monomials": s.nmon, "status": hc.STATUS_NAMES[st["status"]],
+    hc.hc_set_track_tiles(0, 0, 0, 0)
+    return {"n": s.n, "monomials": s.nmon, "grid_chunk": chunk["grid_chunk"], "status": hc.STATUS_NAMES[st["status"]],
             "stages": int(st["n_corr"]), "accepted": int(st["n_succ"]), "newton_its": int(st["newton_its"]),
             "t_end": st["t_end"], "min_step": st["min_step"], "seconds": dt, "stages_per_s": st["n_corr"] / dt,
             "max_abs_z_end": float(np.abs(z[:, 0, 0] + 1j * z[:, 1, 0]).max())}
@@ -341,9 +362,15 @@ def single_path_bench(torch, hc, synth):
     (corrector stages) per second and microseconds per stage; the end point's agreement with
     the oracle is checked in tests/test_gpu_track.py."""
     import numpy as np
+    from paper_1109_0545_gb300 import autotune
     s, g = synth.single_path_dd(1)
     h = hc.system_from(s, 2, g)
     out = {"n": s.n, "monomials": s.nmon}
+    xt = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 2)])).cuda()
+    tiles = autotune.tune_track([h], xt, hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE,
+                                                                  predictor=hc.HC_PRED_QUADRATIC),
+                                use_cache=False, candidates=[(64, 0, 0), (128, 0, 0), (256, 0, 0)])
+    out["threads_per_block"] = tiles["threads_per_block"]
     for name, kw in (("plain_all_dd_secant", dict(lu_mode=hc.HC_LU_NATIVE)),
                      ("fp64_refine_quadratic", dict(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC))):
         x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(s.n), 2)])).cuda()
@@ -359,6 +386,7 @@ def single_path_bench(torch, hc, synth):
                      "path_steps_per_s": st["n_corr"] / dt, "us_per_step": 1e6 * dt / max(st["n_corr"], 1),
                      "seconds": dt}
     h.free()
+    hc.hc_set_track_tiles(0, 0, 0, 0)
     return out
 
 
@@ -588,7 +616,7 @@ def compact_extras(ex: dict) -> dict:
         if not isinstance(res, dict) or "batched_all_dd_secant" not in res:
             continue
         key = "paths_per_s" if fam == "uneven_regular" else "path_steps_per_s"
-        row = {"unit": key, "paths": res["paths"], "cap": res.get("stage_cap"),
+        row = {"unit": key, "paths": res["paths"], "cap": res.get("stage_cap"), "tiles": res.get("tiles"),
                "plain_1_per_launch": r(res["plain_one_path_per_launch"][key]),
                "plain_sample_paths": res["plain_one_path_per_launch"]["sample_paths"],
                "batched_all_dd": r(res["batched_all_dd_secant"][key])}
@@ -604,8 +632,8 @@ def compact_extras(ex: dict) -> dict:
         out["tracker_uneven_8192"] = {"path_steps_per_s": r(tr["uneven_8192_paths"]["path_steps_per_s"])}
     lp = ex.get("large_path_qd_n96")
     if lp:
-        out["large_path_qd_n96"] = {k: (r(v, 6) if isinstance(v, float) else v) for k, v in lp.items()
-                                    if k in ("status", "stages", "seconds", "stages_per_s", "t_end")}
+        out["large_path_qd_n96"] = {k: (r(v, 9) if isinstance(v, float) else v) for k, v in lp.items()
+                                    if k in ("status", "stages", "seconds", "stages_per_s", "t_end", "grid_chunk")}
     sp = ex.get("single_path_n8")
     if sp:
         out["single_path_n8_stages_per_s"] = {k: r(v["path_steps_per_s"]) for k, v in sp.items() if isinstance(v, dict)}

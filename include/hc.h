@@ -136,6 +136,26 @@ int hc_newton_step(hc_system *sys, int npts, double t, double *x, int lu_mode,
  */
 int hc_set_tiles(int rows_per_task, int blocks_per_sm);
 
+/*
+ * hc_set_track_tiles -- execution shape of hc_track_path / hc_track_resume for every
+ * later call in this process (the tracker autotuner's knobs; 0 = automatic):
+ *   threads_per_block  threads of a path's block: 64, 128 (automatic) or 256; the
+ *                      register budget per thread stays that of 512 (double, DD) or 384
+ *                      (QD) threads per SM
+ *   blocks_per_sm      path blocks resident per SM, at most what occupancy allows
+ *   factors            0 or 1: the FP64 factors of a path in shared memory when a block's
+ *                      share of the SM holds them (else global memory); 2: always global
+ *   grid_chunk         contributions per chunk of an entry's sum in HC_TRACK_GRID (32)
+ * Results do not depend on threads_per_block, blocks_per_sm or factors (bit for bit).
+ * grid_chunk changes the order in which the whole-GPU engine adds an entry's
+ * contributions (results within the precision's rounding).  Process-wide host-side
+ * setting, not synchronised with calls in other threads.  Errors: HC_EINVAL.
+ */
+int hc_set_track_tiles(int threads_per_block, int blocks_per_sm, int factors, int grid_chunk);
+
+/* The current settings of hc_set_track_tiles (any pointer may be NULL). */
+int hc_get_track_tiles(int *threads_per_block, int *blocks_per_sm, int *factors, int *grid_chunk);
+
 /* predictors (Sec. 5) and tracker execution modes */
 #define HC_PRED_SECANT 0     /* linear through the last two accepted points */
 #define HC_PRED_QUADRATIC 1  /* per coordinate, the parabola through the last three */

@@ -1,4 +1,4 @@
-"""Autotuner of the evaluation kernel's tile shape.
+"""Autotuners of the evaluation kernel's tile shape and of the path tracker's shape.
 
 The evaluation kernel (one lane per point) splits its work into tasks of one 32-point
 tile times a group of rows, run by persistent warps.  Two knobs set the shape:
@@ -81,6 +81,90 @@ def tune_eval(sysh: "hc.System", x, f, J, npts: int, t: float = 0.5, reps: int =
     hc.hc_set_tiles(best["rows_per_task"], best["blocks_per_sm"])
     out = {"rows_per_task": best["rows_per_task"], "blocks_per_sm": best["blocks_per_sm"],
            "ms": best["ms"], "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    if use_cache:
+        cache[key] = out
+        _save_cache(cache)
+    return dict(out, cached=False, tried=tried)
+
+
+# tracker shapes searched: threads per path block x blocks per SM (0: all that fit) x
+# FP64 factors in shared (0) or global (2) memory
+TRACK_TB = (64, 128, 256)
+TRACK_BPS = (0, 2, 3, 4, 6)
+TRACK_FACTORS = (0, 2)
+GRID_CHUNKS = (16, 32, 64, 128)
+
+
+def _track_key(gpu: str, handles, opts, what: str) -> str:
+    infos = [h.info() for h in handles]
+    ns = sorted(i["n"] for i in infos)
+    shape = (f"{gpu}|{what}|paths{len(handles)}|n{ns[0]}-{ns[-1]}|m{sum(i['nmon'] for i in infos)}"
+             f"|L{infos[0]['prec']}|lu{opts.lu_mode}|pred{opts.predictor}|cap{opts.max_steps}")
+    return hashlib.sha1(shape.encode()).hexdigest()[:16] + "|" + shape
+
+
+def tune_track(handles, x0, opts, reps: int = 1, use_cache: bool = True, candidates=None) -> dict:
+    """Pick (threads_per_block, blocks_per_sm, factors) of the block engine by timing
+    hc_track_path on the caller's own paths (handles, start points x0, options; a stage
+    cap in opts.max_steps keeps the sample short), then apply it with hc_set_track_tiles.
+    Every candidate computes the same results bit for bit (tested).  Returns the choice,
+    its seconds and the candidates tried."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    key = _track_key(gpu, handles, opts, "block")
+    cache = _load_cache() if use_cache else {}
+    prev = hc.hc_get_track_tiles()
+    if key in cache:
+        best = cache[key]
+        hc.hc_set_track_tiles(best["threads_per_block"], best["blocks_per_sm"], best["factors"], prev["grid_chunk"])
+        return dict(best, cached=True)
+    cands = candidates or [(t, b, f) for t in TRACK_TB for b in TRACK_BPS for f in TRACK_FACTORS]
+    x1 = torch.zeros_like(x0)
+    tried = []
+    for t, b, f in cands:
+        hc.hc_set_track_tiles(t, b, f, prev["grid_chunk"])
+        best_s = 1e30
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hc.hc_track_path(handles, x0, x1, opts)
+            best_s = min(best_s, time.perf_counter() - t0)
+        tried.append({"threads_per_block": t, "blocks_per_sm": b, "factors": f, "s": best_s})
+    best = min(tried, key=lambda d: d["s"])
+    hc.hc_set_track_tiles(best["threads_per_block"], best["blocks_per_sm"], best["factors"], prev["grid_chunk"])
+    out = {k: best[k] for k in ("threads_per_block", "blocks_per_sm", "factors", "s")}
+    out["when"] = time.strftime("%Y-%m-%dT%H:%M:%S")
+    if use_cache:
+        cache[key] = out
+        _save_cache(cache)
+    return dict(out, cached=False, tried=tried)
+
+
+def tune_grid_chunk(handle, x0, opts, use_cache: bool = True, candidates=GRID_CHUNKS) -> dict:
+    """Pick the whole-GPU engine's chunk length by timing a few stages of hc_track_path
+    (HC_TRACK_GRID, opts.max_steps stages) on the caller's path; applied with
+    hc_set_track_tiles.  Returns the choice, its seconds and the candidates tried."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    key = _track_key(gpu, [handle], opts, "grid")
+    cache = _load_cache() if use_cache else {}
+    prev = hc.hc_get_track_tiles()
+    if key in cache:
+        best = cache[key]
+        hc.hc_set_track_tiles(prev["threads_per_block"], prev["blocks_per_sm"], prev["factors"], best["grid_chunk"])
+        return dict(best, cached=True)
+    x1 = torch.zeros_like(x0)
+    tried = []
+    for c in candidates:
+        hc.hc_set_track_tiles(prev["threads_per_block"], prev["blocks_per_sm"], prev["factors"], c)
+        hc.hc_track_path([handle], x0, x1, opts)      # warm-up (graph capture, allocation)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hc.hc_track_path([handle], x0, x1, opts)
+        tried.append({"grid_chunk": c, "s": time.perf_counter() - t0})
+    best = min(tried, key=lambda d: d["s"])
+    hc.hc_set_track_tiles(prev["threads_per_block"], prev["blocks_per_sm"], prev["factors"], best["grid_chunk"])
+    out = {"grid_chunk": best["grid_chunk"], "s": best["s"], "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
     if use_cache:
         cache[key] = out
         _save_cache(cache)

@@ -9,10 +9,19 @@
 //     powers (1 block)                   x_j^e
 //     monomials (grid)                   values and partials of every monomial -> V
 //     entries (grid)                     sums per Jacobian entry + homotopy -> H, J
-//     factor (1 block)                   residual, FP64 LU with partial pivoting, dz_0
-//     max_refine x [residual rows (grid), solve (1 block)]    refinement in L limbs
+//     lu (1 block of 1024)               residual, FP64 LU with partial pivoting
+//     inverse (n warps)                  the FP64 inverse, one column per warp
+//     apply (1 block)                    dz_0 = inverse x (-h)
+//     max_refine x [residual rows (n warps), apply (1 block)]   refinement in L limbs
 //     update (1 block)                   z += dz, convergence test
 //   end (1 block)                        accept / step back, step size, stop tests
+//
+// The refinement applies the explicit inverse of the FP64 factors (n triangular solves
+// in parallel, once per factorisation) instead of a triangular solve per sweep: each
+// sweep's correction is then a matrix-vector product of a few microseconds, where one
+// warp's substitution took a quarter of a millisecond.  Like the factors it stands in for,
+// the inverse is an FP64 approximation of J^-1; the sweeps converge to the same solution
+// in L limbs.
 //
 // The control flow of the method is data dependent; every kernel first reads the stage
 // state and returns at once when its work is not needed (the corrector converged, the
@@ -25,8 +34,6 @@
 #include "track.cuh"
 
 #include <vector>
-
-#define HC_GCHUNK 32  // contributions per chunk of an entry's sum
 
 namespace hc {
 
@@ -41,8 +48,9 @@ struct GArgs {
     GStage *g;
     const double *x0;
     double *z, *zp, *zpp, *zh, *ZP, *PW, *V, *HS, *H, *JH, *B, *RV, *DZ;
+    double *INV;              // [2][n][n] the inverse of the FP64 factors, column-major
     int32_t *PIV;
-    // the entries' contribution lists cut into chunks of at most HC_GCHUNK, summed in
+    // the entries' contribution lists cut into chunks of at most `chunk`, summed in
     // parallel (k_g_chunks), then per entry in chunk order (k_g_entries)
     const int32_t *cbeg;      // [nchunks+1] chunk c covers tlist[cbeg[c] .. cend[c])
     const int32_t *cend;
@@ -74,7 +82,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
     __syncthreads();
     if (st.phase == 1) {
         double t1, h;
-        stage_predict<L>(a.o, st, n, a.z, a.zp, a.zpp, nullptr, a.zh, a.ZP, t1, h);
+        stage_predict<L, HC_TB>(a.o, st, n, a.z, a.zp, a.zpp, nullptr, a.zh, a.ZP, t1, h);
         if (tid == 0) {
             g.t1 = t1;
             g.h = h;
@@ -144,63 +152,133 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_entries(GArgs a)
     entry_finish<L>(a.S, e, g.t1, acc, a.HS, a.H, a.JH, nullptr);
 }
 
-// residual of the incoming point, FP64 LU, first solve (block_newton's first half)
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_factor(GArgs a, int b_smem)
+#define HC_GLU 1024  // threads of the whole-GPU engine's LU block
+
+// residual of the incoming point and the FP64 LU (block_newton's first part), by one block
+// of 1024 threads: the trailing updates keep all of one SM's warps busy
+template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu(GArgs a, int b_smem)
 {
     __shared__ BlockShared sh;
-    extern __shared__ double ysh[];  // [2][n], then (b_smem) the factors [2][n][n]
+    extern __shared__ double fsh[];  // (b_smem) the factors [2][n][n]
     GStage &g = *a.g;
     if (!g_active(g)) return;
     const int n = a.S.n, tid = threadIdx.x;
-    double r2 = 0.0;
+    double r2 = 0.0, xn = 0.0;
     int fin = 1;
-    for (int i = tid; i < n; i += HC_TB) {
+    for (int i = tid; i < n; i += HC_GLU) {
         double re, im;
         ld_lead<L>(a.H, n, i, re, im);
         const double v = add_(mul_(re, re), mul_(im, im));
         if (!isfinite(v)) fin = 0;
         r2 = fmax(r2, v);
+        ld_lead<L>(a.zh, n, i, re, im);
+        xn = fmax(xn, sqrt(add_(mul_(re, re), mul_(im, im))));
     }
     fin = block_and(fin, sh);
-    const double res = sqrt(block_max(r2, sh));
+    block_max2<HC_GLU>(r2, xn, sh);
+    const double res = sqrt(r2);
     double cond = 0.0;
-    double *Bf = b_smem ? ysh + 2 * n : a.B;
-    int status = fin ? block_lu64<L>(n, a.JH, Bf, a.PIV, sh, &cond) : HC_NONFINITE;
+    double *Bf = b_smem ? fsh : a.B;
+    const int status = fin ? block_lu64<L, HC_GLU>(n, a.JH, Bf, a.PIV, sh, &cond) : HC_NONFINITE;
     if (status == HC_OK && b_smem) {
-        // the factors for the refinement solves of the later kernels
-        for (int q = tid; q < 2 * n * n; q += HC_TB) a.B[q] = Bf[q];
-    }
-    if (status == HC_OK) {
-        for (int i = tid; i < n; i += HC_TB) {
-            double re, im;
-            ld_lead<L>(a.H, n, i, re, im);
-            a.RV[i] = -re;
-            a.RV[n + i] = -im;
-        }
-        __syncthreads();
-        if (tid < 32) warp_lu64_solve(n, Bf, a.PIV, a.RV, ysh);
-        __syncthreads();
-        double xn = 0.0;
-        for (int i = tid; i < n; i += HC_TB) {
-            st_c<L>(a.DZ, n, i, c_from<L>(ysh[i], ysh[n + i]));
-            double re, im;
-            ld_lead<L>(a.zh, n, i, re, im);
-            xn = fmax(xn, sqrt(add_(mul_(re, re), mul_(im, im))));
-        }
-        xn = block_max(xn, sh);
-        if (tid == 0) g.xn = xn;
+        // the factors for the inverse
+        for (int q = tid; q < 2 * n * n; q += HC_GLU) a.B[q] = Bf[q];
     }
     if (tid == 0) {
         g.res = res;
         if (g.res_first < 0) g.res_first = res;
         g.cond = cond;
+        g.xn = xn;
         if (status != HC_OK) {
             g.it++;
             g.nst = status;
         } else {
-            g.refine_active = a.o.max_refine > 0;
+            g.refine_active = 0;
             g.prev_dn = INFINITY;
             g.sweeps = 0;
+        }
+    }
+}
+
+// column j = blockIdx.x of the inverse of the FP64 factors: the solve of e_j by one warp
+// (warp_lu64_solve), from a shared-memory copy of the factors when they fit
+template <int L> __global__ void __launch_bounds__(32) k_g_inverse(GArgs a, int b_smem)
+{
+    extern __shared__ double ish[];  // e_j [2][n], y [2][n], then (b_smem) the factors
+    const GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int n = a.S.n, j = blockIdx.x, lane = threadIdx.x;
+    double *ej = ish, *y = ish + 2 * n;
+    const double *Bf = a.B;
+    if (b_smem) {
+        double *Bs = ish + 4 * n;
+        for (int q = lane; q < 2 * n * n; q += 32) Bs[q] = a.B[q];
+        Bf = Bs;
+    }
+    for (int q = lane; q < 2 * n; q += 32) ej[q] = q == j ? 1.0 : 0.0;
+    __syncwarp();
+    warp_lu64_solve(n, Bf, a.PIV, ej, y);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        a.INV[(size_t)j * n + i] = y[i];
+        a.INV[(size_t)n * n + (size_t)j * n + i] = y[n + i];
+    }
+}
+
+// d = INV r in FP64: 8 lanes per row, each summing the columns j = lane (mod 8) in order,
+// then a fixed shuffle tree.  first: r = -h (the first solve), dz = d; else r = the
+// residual of k_g_refine_rows, dz += d, and the refinement's stop test:
+// ||d|| <= 2^(-53 L) max(||x||, ||dz||), ||d|| no longer shrinking, or max_refine sweeps
+#define HC_GAPPLY 1024
+template <int L> __global__ void __launch_bounds__(HC_GAPPLY, 1) k_g_apply(GArgs a, int first)
+{
+    __shared__ BlockShared sh;
+    __shared__ double rsh[2 * 256];
+    GStage &g = *a.g;
+    if (!g_active(g) || (!first && !g.refine_active)) return;
+    const int n = a.S.n, tid = threadIdx.x;
+    for (int i = tid; i < n; i += HC_GAPPLY) {
+        if (first) {
+            double re, im;
+            ld_lead<L>(a.H, n, i, re, im);
+            rsh[i] = -re;
+            rsh[n + i] = -im;
+        } else {
+            rsh[i] = a.RV[i];
+            rsh[n + i] = a.RV[n + i];
+        }
+    }
+    __syncthreads();
+    const size_t ip = (size_t)n * n;
+    const int q = tid & 7, rows = HC_GAPPLY / 8;
+    double dn = 0.0, zz = 0.0;
+    for (int base = 0; base < n; base += rows) {
+        const int i = base + (tid >> 3);
+        cdv d = {0.0, 0.0};
+        if (i < n)
+            for (int j = q; j < n; j += 8)
+                d = cdv_fnma(d, cdv{-a.INV[(size_t)j * n + i], -a.INV[ip + (size_t)j * n + i]}, cdv{rsh[j], rsh[n + j]});
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            d.re = add_(d.re, __shfl_xor_sync(0xffffffffu, d.re, o));
+            d.im = add_(d.im, __shfl_xor_sync(0xffffffffu, d.im, o));
+        }
+        if (i < n && q == 0) {
+            const C<L> v = first ? c_from<L>(d.re, d.im) : c_add(ld_c<L>(a.DZ, n, i), c_from<L>(d.re, d.im));
+            st_c<L>(a.DZ, n, i, v);
+            dn = fmax(dn, sqrt(add_(mul_(d.re, d.re), mul_(d.im, d.im))));
+            zz = fmax(zz, sqrt(c_abs2_lead(v)));
+        }
+    }
+    block_max2<HC_GAPPLY>(dn, zz, sh);
+    if (tid == 0) {
+        if (first) {
+            g.refine_active = a.o.max_refine > 0;
+        } else {
+            g.sweeps++;
+            const double tol = ldexp(1.0, -53 * L);
+            if (dn <= tol * fmax(g.xn, zz) || dn >= g.prev_dn || g.sweeps >= a.o.max_refine) g.refine_active = 0;
+            g.prev_dn = dn;
         }
     }
 }
@@ -233,40 +311,6 @@ template <int L> __global__ void __launch_bounds__(32) k_g_refine_rows(GArgs a)
     }
 }
 
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_refine_solve(GArgs a, int b_smem)
-{
-    __shared__ BlockShared sh;
-    extern __shared__ double ysh[];  // [2][n], then (b_smem) a copy of the factors [2][n][n]
-    GStage &g = *a.g;
-    if (!g_active(g) || !g.refine_active) return;
-    const int n = a.S.n, tid = threadIdx.x;
-    // the solve's column walks are dependent loads: from shared memory, not L2
-    const double *Bf = a.B;
-    if (b_smem) {
-        double *Bs = ysh + 2 * n;
-        for (int q = tid; q < 2 * n * n; q += HC_TB) Bs[q] = a.B[q];
-        __syncthreads();
-        Bf = Bs;
-    }
-    if (tid < 32) warp_lu64_solve(n, Bf, a.PIV, a.RV, ysh);
-    __syncthreads();
-    double dn = 0.0, zz = 0.0;
-    for (int i = tid; i < n; i += HC_TB) {
-        const double dr = ysh[i], di = ysh[n + i];
-        const C<L> v = c_add(ld_c<L>(a.DZ, n, i), c_from<L>(dr, di));
-        st_c<L>(a.DZ, n, i, v);
-        dn = fmax(dn, sqrt(add_(mul_(dr, dr), mul_(di, di))));
-        zz = fmax(zz, sqrt(c_abs2_lead(v)));
-    }
-    block_max2(dn, zz, sh);
-    if (tid == 0) {
-        g.sweeps++;
-        const double tol = ldexp(1.0, -53 * L);
-        if (dn <= tol * fmax(g.xn, zz) || dn >= g.prev_dn || g.sweeps >= a.o.max_refine) g.refine_active = 0;
-        g.prev_dn = dn;
-    }
-}
-
 // z += dz (all or nothing), the convergence test of the corrector or of the end game
 template <int L> __global__ void __launch_bounds__(HC_TB) k_g_update(GArgs a)
 {
@@ -284,8 +328,8 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_update(GArgs a)
         zn = fmax(zn, sqrt(c_abs2_lead(v)));
     }
     ok = block_and(ok, sh);
-    dzn = block_max(dzn, sh);
-    zn = block_max(zn, sh);
+    dzn = block_max<HC_TB>(dzn, sh);
+    zn = block_max<HC_TB>(zn, sh);
     if (ok)
         for (int i = tid; i < n; i += HC_TB) st_c<L>(a.zh, n, i, c_add(ld_c<L>(a.zh, n, i), ld_c<L>(a.DZ, n, i)));
     __syncthreads();
@@ -310,7 +354,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_end(GArgs a)
     const GStage g = *a.g;
     const int n = a.S.n, tid = threadIdx.x;
     if (st.phase == 1) {
-        stage_finish<L>(a.o, st, sh, n, a.z, a.zp, a.zpp, a.zh, a.ZP, g.t1, g.h, g.it, g.nst, g.conv, g.res,
+        stage_finish<L, HC_TB>(a.o, st, sh, n, a.z, a.zp, a.zpp, a.zh, a.ZP, g.t1, g.h, g.it, g.nst, g.conv, g.res,
                         g.res_first, g.cond, a.log, a.log_cap, a.log0);
     } else if (st.phase == 2) {
         for (int q = tid; q < 2 * L * n; q += HC_TB) a.z[q] = a.zh[q];
@@ -334,17 +378,16 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
 {
     const int mblocks = (a.S.nmon + HC_TB - 1) / HC_TB;
     const int eblocks = (a.S.npoly * (a.S.n + 1) + HC_TB - 1) / HC_TB;
-    const size_t ysh_bytes = sizeof(double) * 2 * (size_t)a.S.n;  // n <= 256: at most 4 KiB
-    // the FP64 LU and the refinement solves in shared memory when the factors fit (n <= 110)
+    // the FP64 LU, and each column solve of the inverse, from shared memory when the
+    // factors fit (n <= 110)
     const size_t bsm = sizeof(double) * 2 * (size_t)a.S.n * a.S.n;
-    const int b_smem = ysh_bytes + bsm <= 200 * 1024;
-    const size_t fac_bytes = ysh_bytes + (b_smem ? bsm : 0);
-    if (fac_bytes > 48 * 1024) {
-        cudaError_t ea = cudaFuncSetAttribute(k_g_factor<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fac_bytes);
-        if (ea == cudaSuccess)
-            ea = cudaFuncSetAttribute(k_g_refine_solve<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fac_bytes);
-        if (ea != cudaSuccess) return hc_cuda_fail(ea, "k_g_factor shared memory");
-    }
+    const size_t vec4 = sizeof(double) * 4 * (size_t)a.S.n;
+    const int b_smem = vec4 + bsm <= 200 * 1024;
+    const size_t lu_bytes = b_smem ? bsm : 0, inv_bytes = vec4 + (b_smem ? bsm : 0);
+    cudaError_t ea = cudaFuncSetAttribute(k_g_lu<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(lu_bytes > 0 ? lu_bytes : 1));
+    if (ea == cudaSuccess)
+        ea = cudaFuncSetAttribute(k_g_inverse<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_bytes);
+    if (ea != cudaSuccess) return hc_cuda_fail(ea, "whole-GPU engine shared memory");
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return hc_cuda_fail(e, "cudaStreamBeginCapture");
@@ -354,10 +397,12 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
         k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_TB, 0, cs>>>(a);
         k_g_chunks<L><<<(a.nchunks + HC_TB - 1) / HC_TB, HC_TB, 0, cs>>>(a);
         k_g_entries<L><<<eblocks, HC_TB, 0, cs>>>(a);
-        k_g_factor<L><<<1, HC_TB, fac_bytes, cs>>>(a, b_smem);
+        k_g_lu<L><<<1, HC_GLU, lu_bytes, cs>>>(a, b_smem);
+        k_g_inverse<L><<<a.S.n, 32, inv_bytes, cs>>>(a, b_smem);
+        k_g_apply<L><<<1, HC_GAPPLY, 0, cs>>>(a, 1);
         for (int r = 0; r < max_refine; r++) {
             k_g_refine_rows<L><<<a.S.n, 32, 0, cs>>>(a);
-            k_g_refine_solve<L><<<1, HC_TB, fac_bytes, cs>>>(a, b_smem);
+            k_g_apply<L><<<1, HC_GAPPLY, 0, cs>>>(a, 0);
         }
         k_g_update<L><<<1, HC_TB, 0, cs>>>(a);
     }
@@ -377,10 +422,11 @@ void hc_stats_of(const PathState &q, hc_path_stats &r);
 
 // One path per call to this function: workspace, graph, replays, statistics.  With a
 // state (hc_track_resume) the path starts from it, the previous points are the caller's
-// hist (x0 == x1 is the current point), and at most max_stages stages run.
+// hist (x0 == x1 is the current point), and at most max_stages stages run.  An entry's
+// contribution list is summed in chunks of `chunk` (the tracker tiles' grid_chunk).
 int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double *hist,
                        hc_path_state *state, int max_stages, const hc_track_opts *o,
-                       hc_path_stats *stats, hc_step_record *log, int log_cap, cudaStream_t st)
+                       hc_path_stats *stats, hc_step_record *log, int log_cap, int chunk, cudaStream_t st)
 {
     const int n = s->n, L = s->prec;
     const size_t vec = sizeof(double) * 2 * L * (size_t)n;
@@ -391,7 +437,8 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     const size_t o_zp = put(vec), o_zpp = put(vec), o_zh = put(vec), o_ZP = put(vec);
     const size_t o_pw = put(vec * (s->max_exp > 2 ? s->max_exp - 2 : 1));
     const size_t o_v = put(sizeof(double) * 2 * L * (vplane > 0 ? vplane : 1));
-    const size_t o_hs = put(3 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n);
+    const size_t o_hs = put(3 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n),
+                 o_inv = put(sizeof(double) * 2 * (size_t)n * n);
     const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n);
     // chunks of the entries' contribution lists (from the transpose table's offsets)
     const int ne = s->npoly * (n + 1);
@@ -400,7 +447,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     for (int e = 0; e < ne; e++) {
         int r = tptr[e];
         do {
-            const int r1 = r + HC_GCHUNK < tptr[e + 1] ? r + HC_GCHUNK : tptr[e + 1];
+            const int r1 = r + chunk < tptr[e + 1] ? r + chunk : tptr[e + 1];
             cbeg.push_back(r);
             cend.push_back(r1);
             r = r1;
@@ -429,6 +476,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     a.H = (double *)(b + o_h);
     a.JH = (double *)(b + o_jh);
     a.B = (double *)(b + o_b);
+    a.INV = (double *)(b + o_inv);
     a.RV = (double *)(b + o_rv);
     a.DZ = (double *)(b + o_dz);
     a.PIV = (int32_t *)(b + o_piv);

@@ -14,181 +14,18 @@
 #include <algorithm>
 #include <vector>
 
-#include "track.cuh"
+#include "track_kernel.cuh"
 
 namespace hc {
-
-struct SlotLayout {
-    size_t pw, v, hs, ht, h, jh, b, dz, zp, stride;
-};
-
-struct TrackArgs {
-    const DevSys *sys;        // [npaths]
-    const long long *xoff;    // [npaths] offset (doubles) of path p in x0/x1
-    const double *x0;
-    double *x1;
-    double *hist;             // per path at 3 xoff[p]: previous accepted point, second
-                              // previous, tangent (each 2 L n doubles)
-    double *zh;               // per path at xoff[p]: the predicted, then corrected point
-    PathState *st;
-    const long long *n0;      // [npaths] corrector stages done before this call (log
-                              // offset and stage budget of the call)
-    hc_track_opts o;
-    char *slots;
-    SlotLayout lay;
-    int *queue;
-    int *active;              // paths that may still advance in this call
-    const int *order;         // [npaths] paths in the order they are taken: largest
-                              // evaluation cost first, so the last ones to start are short
-    hc_step_record *log;
-    int log_cap;
-    int npaths;
-    int nmax;                 // largest n of the batch
-    int b_smem;               // the FP64 factors in shared memory (else in the slot)
-    int max_stages;           // corrector stages per path in this call
-};
-
-// Dynamic shared memory of a tracking block, in doubles: Y, RV [2][nmax] each, PIV
-// [nmax] ints, then (b_smem) the FP64 factors B [2][nmax][nmax].
-__host__ __device__ __forceinline__ size_t track_smem_doubles(int nmax, int b_smem)
-{
-    return 4 * (size_t)nmax + (size_t)(nmax + 1) / 2 + (b_smem ? 2 * (size_t)nmax * nmax : 0);
-}
-
-template <int L> __device__ __forceinline__ Slot<L> slot_of(const TrackArgs &a, int b, double *dsm)
-{
-    char *base = a.slots + (size_t)b * a.lay.stride;
-    Slot<L> w;
-    w.PW = (double *)(base + a.lay.pw);
-    w.V = (double *)(base + a.lay.v);
-    w.HS = (double *)(base + a.lay.hs);
-    w.HT = a.o.predictor == HC_PRED_TANGENT ? (double *)(base + a.lay.ht) : nullptr;
-    w.H = (double *)(base + a.lay.h);
-    w.JH = (double *)(base + a.lay.jh);
-    w.DZ = (double *)(base + a.lay.dz);
-    w.ZP = (double *)(base + a.lay.zp);
-    w.Y = dsm;
-    w.RV = dsm + 2 * a.nmax;
-    w.PIV = (int32_t *)(dsm + 4 * a.nmax);
-    w.B = a.b_smem ? dsm + 4 * (size_t)a.nmax + (a.nmax + 1) / 2 : (double *)(base + a.lay.b);
-    return w;
-}
-
-
-//
-// Advance path p by at most max_stages corrector stages (then its end game, once t = 1),
-// within the call's budget of a.max_stages stages per path.
-// Every thread keeps the same copy of the path's scalars: each decision is taken from
-// values that block reductions broadcast, so all threads follow the same branch.
-//
-template <int L>
-__device__ void path_run(const TrackArgs &a, int p, const Slot<L> &w, BlockShared &sh, int max_stages)
-{
-    const DevSys S = a.sys[p];
-    const hc_track_opts &o = a.o;
-    const int n = S.n, tid = threadIdx.x;
-    double *z = a.x1 + a.xoff[p];
-    double *zp = a.hist + 3 * a.xoff[p];
-    double *zpp = zp + 2 * L * n;
-    double *tv = zpp + 2 * L * n;  // [2][n] dx/dt at the last accepted point (tangent predictor)
-    double *zh = a.zh + a.xoff[p];
-    const bool tangent = o.predictor == HC_PRED_TANGENT;
-    PathState st = a.st[p];
-    const long long n0 = a.n0[p];
-    // done, or this call's stages spent (the path was counted out of `active` then)
-    if (st.phase == 3 || (st.phase == 1 && st.n_corr - n0 >= a.max_stages)) return;
-    if (st.phase == 0) {
-        for (int q = tid; q < 2 * L * n; q += HC_TB) z[q] = a.x0[a.xoff[p] + q];
-        path_init(st, o, p);
-        __syncthreads();
-    }
-    hc_step_record *log = a.log ? a.log + (size_t)p * a.log_cap : nullptr;
-    int stages = 0;
-    while (st.phase == 1 && stages < max_stages && st.n_corr - n0 < a.max_stages) {
-        double t1, h;
-        stage_predict<L>(o, st, n, z, zp, zpp, tv, zh, w.ZP, t1, h);
-        // corrector: Alg. 4.1
-        double res = 1.0, res_first = -1.0, cond = 0.0;
-        int it = 0, nst = HC_OK, conv = 0;
-        while (!conv && it < o.max_it) {
-            const NewtonOut no = block_newton<L>(S, zh, t1, o.lu_mode, o.max_refine, w, sh);
-            res = no.res;
-            if (res_first < 0) res_first = res;
-            it++;
-            nst = no.status;
-            cond = no.cond;
-            if (nst != HC_OK) break;
-            conv = (res <= o.eps) || (no.dzn <= o.eps_x * (no.zn > 1.0 ? no.zn : 1.0));
-        }
-        // tangent at the corrected point: dx/dt = -J^-1 dh/dt from the last iteration's
-        // evaluation and FP64 factors, kept if the stage is accepted
-        if (tangent && conv && nst == HC_OK) {
-            if (tid < 32) warp_lu64_solve(n, w.B, w.PIV, w.HT, w.Y);
-            __syncthreads();
-        }
-        const long long succ0 = st.n_succ;
-        stage_finish<L>(o, st, sh, n, z, zp, zpp, zh, w.ZP, t1, h, it, nst, conv, res, res_first, cond,
-                        log, a.log_cap, n0);
-        if (tangent && st.n_succ > succ0) {
-            for (int q = tid; q < 2 * n; q += HC_TB) tv[q] = -w.Y[q];
-            __syncthreads();
-        }
-        stages++;
-    }
-    if (st.phase == 2) {
-        // end game at t = 1: Newton on f until converged with the end tolerances
-        double res = 1.0;
-        int conv = 0;
-        while (!conv && st.end_its < o.end_it) {
-            const NewtonOut no = block_newton<L>(S, z, 1.0, o.lu_mode, o.max_refine, w, sh);
-            st.end_its++;
-            res = no.res;
-            if (no.status != HC_OK) {
-                st.status = no.status;
-                break;
-            }
-            conv = (res <= o.eps_end) || (no.dzn <= o.eps_end_x * (no.zn > 1.0 ? no.zn : 1.0));
-        }
-        st.res_end = res;
-        if (st.status == HC_OK && !conv) st.status = HC_NOCONV;
-        st.phase = 3;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        a.st[p] = st;
-        if (st.phase == 3 || st.n_corr - n0 >= a.max_stages) atomicSub(a.active, 1);
-    }
-    __syncthreads();
-}
-
-template <int L>
-__global__ void __launch_bounds__(HC_TB, L == 4 ? 3 : 4) k_track(TrackArgs a, int persistent)
-{
-    __shared__ BlockShared sh;
-    __shared__ int s_p;
-    extern __shared__ double dsm[];
-    const Slot<L> w = slot_of<L>(a, blockIdx.x, dsm);
-    if (persistent) {
-        for (;;) {
-            if (threadIdx.x == 0) s_p = atomicAdd(a.queue, 1);
-            __syncthreads();
-            const int q = s_p;
-            __syncthreads();
-            if (q >= a.npaths) break;
-            path_run<L>(a, a.order[q], w, sh, 0x7fffffff);
-        }
-    } else {
-        for (int q = blockIdx.x; q < a.npaths; q += gridDim.x) path_run<L>(a, a.order[q], w, sh, 1);
-    }
-}
-
+HC_TRACK_INSTANTIATE(128)
 }  // namespace hc
+
 
 using namespace hc;
 
 int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double *hist,
                        hc_path_state *state, int max_stages, const hc_track_opts *o,
-                       hc_path_stats *stats, hc_step_record *log, int log_cap, cudaStream_t st);
+                       hc_path_stats *stats, hc_step_record *log, int log_cap, int chunk, cudaStream_t st);
 
 extern "C" void hc_track_opts_default(hc_track_opts *o)
 {
@@ -248,20 +85,53 @@ static int check_opts(const hc_track_opts *o)
     return HC_SUCCESS;
 }
 
-template <int L>
-static int launch_track(TrackArgs &a, int grid, int persistent, size_t smem, cudaStream_t st)
+// Tiles of the tracker (hc_set_track_tiles), process-wide; 0 = automatic.
+static int g_track_tb = 0;       // threads per path block: 64, 128 or 256
+static int g_track_bps = 0;      // path blocks per SM (capped by occupancy)
+static int g_track_factors = 0;  // 0/1: FP64 factors in shared memory when they fit; 2: global
+static int g_grid_chunk = 0;     // contributions per chunk of the whole-GPU engine's entry sums
+
+template <int L> static int launch_track(int tb, TrackArgs &a, int grid, int persistent, size_t smem, cudaStream_t st)
 {
-    k_track<L><<<grid, HC_TB, smem, st>>>(a, persistent);
+    return tb == 64 ? track_launch<L, 64>(a, grid, persistent, smem, st)
+         : tb == 256 ? track_launch<L, 256>(a, grid, persistent, smem, st)
+                     : track_launch<L, 128>(a, grid, persistent, smem, st);
+}
+
+template <int L> static int occupancy_track(int tb, size_t smem)
+{
+    return tb == 64 ? track_occupancy<L, 64>(smem) : tb == 256 ? track_occupancy<L, 256>(smem)
+                                                   : track_occupancy<L, 128>(smem);
+}
+
+static int launch_track_any(int L, int tb, TrackArgs &a, int grid, int persistent, size_t smem, cudaStream_t st)
+{
+    return L == 1 ? launch_track<1>(tb, a, grid, persistent, smem, st)
+         : L == 2 ? launch_track<2>(tb, a, grid, persistent, smem, st)
+                  : launch_track<4>(tb, a, grid, persistent, smem, st);
+}
+
+extern "C" int hc_set_track_tiles(int threads_per_block, int blocks_per_sm, int factors, int grid_chunk)
+{
+    if (threads_per_block != 0 && threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256)
+        return hc_fail(HC_EINVAL, "threads_per_block must be 0, 64, 128 or 256");
+    if (blocks_per_sm < 0 || blocks_per_sm > 32) return hc_fail(HC_EINVAL, "blocks_per_sm out of [0, 32]");
+    if (factors < 0 || factors > 2) return hc_fail(HC_EINVAL, "factors must be 0, 1 or 2");
+    if (grid_chunk < 0 || grid_chunk > 4096) return hc_fail(HC_EINVAL, "grid_chunk out of [0, 4096]");
+    g_track_tb = threads_per_block;
+    g_track_bps = blocks_per_sm;
+    g_track_factors = factors;
+    g_grid_chunk = grid_chunk;
     return HC_SUCCESS;
 }
 
-// blocks per SM at this dynamic shared memory size (which is opted into first)
-template <int L> static int occupancy_track(size_t smem)
+extern "C" int hc_get_track_tiles(int *threads_per_block, int *blocks_per_sm, int *factors, int *grid_chunk)
 {
-    cudaFuncSetAttribute(k_track<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_track<L>, HC_TB, smem);
-    return occ < 1 ? 1 : occ;
+    if (threads_per_block) *threads_per_block = g_track_tb;
+    if (blocks_per_sm) *blocks_per_sm = g_track_bps;
+    if (factors) *factors = g_track_factors;
+    if (grid_chunk) *grid_chunk = g_grid_chunk;
+    return HC_SUCCESS;
 }
 
 struct DevBuf {
@@ -333,21 +203,25 @@ static int track_impl(hc_system *const *sys, int npaths, const double *x0, doubl
             rc = hc_track_grid_path(sys[p], x0 + off[p], x1 + off[p], hist_io ? hist_io + 3 * off[p] : nullptr,
                                     state_io ? &state_io[p] : nullptr, max_stages, opts, stats ? &stats[p] : &tmp,
                                     log_cap > 0 ? log + (size_t)p * log_cap : nullptr, log_cap,
-                                    (cudaStream_t)stream);
+                                    g_grid_chunk ? g_grid_chunk : 32, (cudaStream_t)stream);
             if (rc) return rc;
         }
         return HC_SUCCESS;
     }
     const int sms = hc_num_sms();
-    // the FP64 factors go to shared memory when a block's share stays within what the
-    // register limit's blocks per SM leave of the SM's 228 KiB: four blocks (128 registers)
-    // for double and DD, 54 KiB each; three for QD (168 registers), 72 KiB each.  With four
-    // blocks and the factors in global memory the tracker still runs 8 % more stages per
-    // second than with three and the factors in shared memory (uneven family, n <= 64).
-    const size_t smem_cap = L == 4 ? 72 * 1024 : 54 * 1024;
-    const int b_smem = sizeof(double) * track_smem_doubles(nmax, 1) <= smem_cap;
+    const int tb = g_track_tb ? g_track_tb : 128;
+    // The FP64 factors go to shared memory when a block's share stays within what the
+    // blocks the register budget allows per SM leave of the SM's 228 KiB: 512 (double, DD)
+    // or 384 (QD) threads per SM, e.g. four 128-thread blocks of 54 KiB or three QD blocks
+    // of 72 KiB.  (With four 128-thread blocks and the factors in global memory the tracker
+    // still runs 8 % more stages per second than with three and the factors in shared
+    // memory: uneven family, n <= 64.)  hc_set_track_tiles can keep them in global memory.
+    const int reg_blocks = ((L == 4 ? 384 : 512) / tb) > 0 ? (L == 4 ? 384 : 512) / tb : 1;
+    const size_t smem_cap = 228 * 1024 / reg_blocks - 3 * 1024;
+    const int b_smem = g_track_factors != 2 && sizeof(double) * track_smem_doubles(nmax, 1) <= smem_cap;
     const size_t smem = sizeof(double) * track_smem_doubles(nmax, b_smem);
-    int occ = L == 1 ? occupancy_track<1>(smem) : L == 2 ? occupancy_track<2>(smem) : occupancy_track<4>(smem);
+    int occ = L == 1 ? occupancy_track<1>(tb, smem) : L == 2 ? occupancy_track<2>(tb, smem) : occupancy_track<4>(tb, smem);
+    if (g_track_bps > 0 && g_track_bps < occ) occ = g_track_bps;
     const int grid = (int)(npaths < (long long)sms * occ ? npaths : (long long)sms * occ);
 
     SlotLayout lay;
@@ -449,9 +323,7 @@ static int track_impl(hc_system *const *sys, int npaths, const double *x0, doubl
     HC_CUDA_TRY(cudaMemcpyAsync(ctr, hctr, sizeof hctr, cudaMemcpyHostToDevice, st));
 
     if (opts->mode == HC_TRACK_PERSISTENT) {
-        if (L == 1) launch_track<1>(a, grid, 1, smem, st);
-        else if (L == 2) launch_track<2>(a, grid, 1, smem, st);
-        else launch_track<4>(a, grid, 1, smem, st);
+        launch_track_any(L, tb, a, grid, 1, smem, st);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return hc_cuda_fail(e, "k_track launch");
     } else if (h_active > 0) {
@@ -467,9 +339,7 @@ static int track_impl(hc_system *const *sys, int npaths, const double *x0, doubl
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             for (int g = 0; g < opts->graph_steps; g++) {
-                if (L == 1) launch_track<1>(a, grid, 0, smem, cs);
-                else if (L == 2) launch_track<2>(a, grid, 0, smem, cs);
-                else launch_track<4>(a, grid, 0, smem, cs);
+                launch_track_any(L, tb, a, grid, 0, smem, cs);
             }
             e = cudaStreamEndCapture(cs, &graph);
         }

@@ -1,0 +1,7 @@
+// hc_track_tb64.cu -- the block engine of the path tracker with 64-thread blocks (its
+// own translation unit, so the instances compile in parallel).
+#include "track_kernel.cuh"
+
+namespace hc {
+HC_TRACK_INSTANTIATE(64)
+}  // namespace hc

@@ -6,8 +6,9 @@
 
 namespace hc {
 
-#define HC_TB 128          // threads per path block
-#define HC_TW (HC_TB / 32)
+#define HC_TB 128          // threads per block of the whole-GPU engine's kernels; the block
+                           // engine's default (its block size is the template parameter TB)
+#define HC_TWMAX 32        // warps of the largest block using the block reductions (1024)
 
 // per-slot scratch of one block (global memory sized for the largest system; the solve's
 // vectors, and the FP64 factors where they fit, in shared memory)
@@ -28,9 +29,9 @@ template <int L> struct Slot {
 };
 
 struct BlockShared {
-    double rv[HC_TW];
-    double rv2[HC_TW];
-    int ri[HC_TW];
+    double rv[HC_TWMAX];
+    double rv2[HC_TWMAX];
+    int ri[HC_TWMAX];
     double bc[4];
     int ibc[4];
 };
@@ -42,21 +43,59 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// max over the block; every thread gets the same value
-__device__ __forceinline__ double block_max(double v, BlockShared &sh)
+// The last step of a block reduction: after the barrier that published each warp's value
+// in sh (rv[w], and ri[w] for an argmax), every warp loads the TB / 32 values into its
+// lanes and reduces them with log2(TB / 32) shuffles, then lane 0's result is broadcast.
+// Looping over the warps instead would cost every thread one FP64 comparison (FP64 pipe)
+// per warp: with 32 warps, more than the work a column of the LU reduces.
+template <int TB> __device__ __forceinline__ double merge_max(const double *rv)
+{
+    constexpr int NW = TB / 32;
+    if (NW == 1) return rv[0];
+    const int lane = threadIdx.x & 31;
+    double m = lane < NW ? rv[lane] : -INFINITY;
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return __shfl_sync(0xffffffffu, m, 0);
+}
+
+// argmax of the published (rv[w], ri[w]), ties to the lowest index
+template <int TB> __device__ __forceinline__ void merge_argmax(const double *rv, const int *ri, double &v, int &i)
+{
+    constexpr int NW = TB / 32;
+    if (NW == 1) {
+        v = rv[0];
+        i = ri[0];
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    v = lane < NW ? rv[lane] : -INFINITY;
+    i = lane < NW ? ri[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (v2 > v || (v2 == v && i2 < i)) {
+            v = v2;
+            i = i2;
+        }
+    }
+    v = __shfl_sync(0xffffffffu, v, 0);
+    i = __shfl_sync(0xffffffffu, i, 0);
+}
+
+// max over the block of TB threads; every thread gets the same value
+template <int TB> __device__ __forceinline__ double block_max(double v, BlockShared &sh)
 {
     v = warp_max(v);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sh.rv[threadIdx.x >> 5] = v;
     __syncthreads();
-    double m = sh.rv[0];
-#pragma unroll
-    for (int w = 1; w < HC_TW; w++) m = fmax(m, sh.rv[w]);
-    return m;
+    return merge_max<TB>(sh.rv);
 }
 
 // two maxima over the block with one pair of barriers
-__device__ __forceinline__ void block_max2(double &a, double &b, BlockShared &sh)
+template <int TB> __device__ __forceinline__ void block_max2(double &a, double &b, BlockShared &sh)
 {
     a = warp_max(a);
     b = warp_max(b);
@@ -66,13 +105,8 @@ __device__ __forceinline__ void block_max2(double &a, double &b, BlockShared &sh
         sh.rv2[threadIdx.x >> 5] = b;
     }
     __syncthreads();
-    a = sh.rv[0];
-    b = sh.rv2[0];
-#pragma unroll
-    for (int w = 1; w < HC_TW; w++) {
-        a = fmax(a, sh.rv[w]);
-        b = fmax(b, sh.rv2[w]);
-    }
+    a = merge_max<TB>(sh.rv);
+    b = merge_max<TB>(sh.rv2);
 }
 
 __device__ __forceinline__ int block_and(int v, BlockShared &sh)
@@ -81,7 +115,7 @@ __device__ __forceinline__ int block_and(int v, BlockShared &sh)
 }
 
 // argmax of (v, i) over the block, ties to the lowest i; every thread gets the winner
-__device__ __forceinline__ void block_argmax(double &v, int &i, BlockShared &sh)
+template <int TB> __device__ __forceinline__ void block_argmax(double &v, int &i, BlockShared &sh)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -98,14 +132,7 @@ __device__ __forceinline__ void block_argmax(double &v, int &i, BlockShared &sh)
         sh.ri[threadIdx.x >> 5] = i;
     }
     __syncthreads();
-    v = sh.rv[0];
-    i = sh.ri[0];
-#pragma unroll
-    for (int w = 1; w < HC_TW; w++)
-        if (sh.rv[w] > v || (sh.rv[w] == v && sh.ri[w] < i)) {
-            v = sh.rv[w];
-            i = sh.ri[w];
-        }
+    merge_argmax<TB>(sh.rv, sh.ri, v, i);
 }
 
 // ------------------------------------------------------------------------------ evaluation
@@ -240,20 +267,20 @@ __device__ __forceinline__ void entry_from_V(const DevSys &S, int e, double t, c
 
 // h(z, t) (or f(z) for t < 0) and its Jacobian by the block; entries are taken in the
 // order of S.eperm (longest contribution lists first)
-template <int L>
+template <int L, int TB>
 __device__ void block_eval(const DevSys &S, const double *__restrict__ z, double t, const Slot<L> &w)
 {
     const int n = S.n, tid = threadIdx.x;
     const C<L> gs = gamma_one_minus_t<L>(S.gre, S.gim, t < 0.0 ? 0.0 : t);
-    for (int j = tid; j < n; j += HC_TB) {
+    for (int j = tid; j < n; j += TB) {
         powers_of<L>(S, j, z, w.PW);
         if (t >= 0.0 && j < S.npoly) homotopy_terms<L>(S, j, z, gs, w.HS, w.HT != nullptr);
     }
     __syncthreads();
-    for (int q = tid; q < S.nmon; q += HC_TB) monomial_to_V<L>(S, __ldg(S.perm + q), z, w.PW, w.V);
+    for (int q = tid; q < S.nmon; q += TB) monomial_to_V<L>(S, __ldg(S.perm + q), z, w.PW, w.V);
     __syncthreads();
     const int ne = S.npoly * (n + 1);
-    for (int q = tid; q < ne; q += HC_TB) entry_from_V<L>(S, __ldg(S.eperm + q), t, w.V, w.HS, w.H, w.JH, w.HT);
+    for (int q = tid; q < ne; q += TB) entry_from_V<L>(S, __ldg(S.eperm + q), t, w.V, w.HS, w.H, w.JH, w.HT);
     __syncthreads();
 }
 
@@ -263,7 +290,7 @@ __device__ void block_eval(const DevSys &S, const double *__restrict__ z, double
 // rows are swapped, the pivot's reciprocal replaces it, multipliers replace the column
 // below it, the trailing block and b are updated; back substitution leaves z = A^-1 b in b.
 // *cond gets log10 of the ratio of the largest to the smallest pivot modulus.
-template <int L>
+template <int L, int TB>
 __device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, BlockShared &sh, double *cond)
 {
     const int tid = threadIdx.x;
@@ -272,7 +299,7 @@ __device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, B
     for (int k = 0; k < n; k++) {
         double bv = -1.0;
         int bi = 0x7fffffff;
-        for (int i = k + tid; i < n; i += HC_TB) {
+        for (int i = k + tid; i < n; i += TB) {
             const C<L> a = ld_c<L>(A, ap, (size_t)i * n + k);
             const double v = c_abs2_lead(a);
             if (v > bv) {
@@ -280,13 +307,13 @@ __device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, B
                 bi = i;
             }
         }
-        block_argmax(bv, bi, sh);
+        block_argmax<TB>(bv, bi, sh);
         if (!(bv > 0.0)) return HC_SINGULAR;
         pmax = fmax(pmax, bv);
         pmin = fmin(pmin, bv);
         const int piv = bi;
         if (piv != k) {
-            for (int j = k + tid; j < n; j += HC_TB) {
+            for (int j = k + tid; j < n; j += TB) {
                 const C<L> t0 = ld_c<L>(A, ap, (size_t)k * n + j);
                 st_c<L>(A, ap, (size_t)k * n + j, ld_c<L>(A, ap, (size_t)piv * n + j));
                 st_c<L>(A, ap, (size_t)piv * n + j, t0);
@@ -301,12 +328,12 @@ __device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, B
         if (tid == 0) st_c<L>(A, ap, (size_t)k * n + k, c_inv(ld_c<L>(A, ap, (size_t)k * n + k)));
         __syncthreads();
         const C<L> inv = ld_c<L>(A, ap, (size_t)k * n + k);
-        for (int i = k + 1 + tid; i < n; i += HC_TB)
+        for (int i = k + 1 + tid; i < n; i += TB)
             st_c<L>(A, ap, (size_t)i * n + k, c_mul(ld_c<L>(A, ap, (size_t)i * n + k), inv));
         __syncthreads();
         const int w = n - k;  // columns k+1..n-1 and b
         const int cnt = (n - k - 1) * w;
-        for (int idx = tid; idx < cnt; idx += HC_TB) {
+        for (int idx = tid; idx < cnt; idx += TB) {
             const int i = k + 1 + idx / w, j = k + 1 + idx % w;
             const C<L> l = ld_c<L>(A, ap, (size_t)i * n + k);
             if (j < n)
@@ -320,7 +347,7 @@ __device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, B
         if (tid == 0) st_c<L>(b, n, i, c_mul(ld_c<L>(b, n, i), ld_c<L>(A, ap, (size_t)i * n + i)));
         __syncthreads();
         const C<L> zi = ld_c<L>(b, n, i);
-        for (int r = tid; r < i; r += HC_TB)
+        for (int r = tid; r < i; r += TB)
             st_c<L>(b, n, r, c_fnma(ld_c<L>(b, n, r), ld_c<L>(A, ap, (size_t)r * n + i), zi));
         __syncthreads();
     }
@@ -340,20 +367,20 @@ __device__ __forceinline__ cdv cdv_fnma(cdv acc, cdv a, cdv b)
 // pivot search, the multipliers, the trailing update and the triangular solves are
 // contiguous), gets L (unit, below the diagonal), U, and the reciprocals of U's diagonal;
 // PIV[k] is the original row that ends in row k (the row swaps composed).
-template <int L>
+template <int L, int TB>
 __device__ int block_lu64(int n, const double *__restrict__ A, double *__restrict__ B, int32_t *__restrict__ PIV,
                           BlockShared &sh, double *cond)
 {
     const int tid = threadIdx.x;
     const size_t ap = (size_t)n * n;
-    for (int q = tid; q < n * n; q += HC_TB) {
+    for (int q = tid; q < n * n; q += TB) {
         const int j = q / n, i = q - j * n;
         double re, im;
         ld_lead<L>(A, ap, (size_t)i * n + j, re, im);
         B[q] = re;
         B[ap + q] = im;
     }
-    for (int q = tid; q < n; q += HC_TB) PIV[q] = q;
+    for (int q = tid; q < n; q += TB) PIV[q] = q;
     __syncthreads();
     auto ld = [&](int i, int j) { return cdv{B[(size_t)j * n + i], B[ap + (size_t)j * n + i]}; };
     auto st = [&](int i, int j, cdv v) { B[(size_t)j * n + i] = v.re; B[ap + (size_t)j * n + i] = v.im; };
@@ -361,14 +388,14 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
     // pivot of column 0
     double bv = -1.0;
     int bi = 0x7fffffff;
-    for (int i = tid; i < n; i += HC_TB) {
+    for (int i = tid; i < n; i += TB) {
         const double v = mag(ld(i, 0));
         if (v > bv) {
             bv = v;
             bi = i;
         }
     }
-    block_argmax(bv, bi, sh);
+    block_argmax<TB>(bv, bi, sh);
     double pmax = 0.0, pmin = INFINITY;
     // Two barriers per column: (A) multipliers and row swap, (B) trailing update, which also
     // finds the next column's pivot (its warps' candidates meet after the barrier)
@@ -379,16 +406,23 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
         const int piv = bi;
         // (A) the pivot row's value moves to row k: multipliers of column k from the rows
         // before the swap (row piv takes the old row k's entry), the other columns swapped
-        const cdv a = ld(piv, k);
-        const cdv inv = {a.re / bv, -a.im / bv};
-        for (int i = k + 1 + tid; i < n; i += HC_TB) st(i, k, cdv_mul(ld(i == piv ? k : i, k), inv));
+        // the pivot's reciprocal conj(a) / |a|^2, formed only by the threads that use it (a
+        // division is a long FP64 sequence: every thread of a large block forming it would
+        // cost more than the factorisation itself)
+        cdv inv = {0.0, 0.0};
+        if (tid == 0 || k + 1 + tid < n) {
+            const cdv a = ld(piv, k);
+            const double r = 1.0 / bv;
+            inv = {a.re * r, -a.im * r};
+        }
+        for (int i = k + 1 + tid; i < n; i += TB) st(i, k, cdv_mul(ld(i == piv ? k : i, k), inv));
         if (piv != k) {
             if (tid == 0) {
                 const int t0 = PIV[k];
                 PIV[k] = PIV[piv];
                 PIV[piv] = t0;
             }
-            for (int j = tid; j < n; j += HC_TB) {
+            for (int j = tid; j < n; j += TB) {
                 if (j == k) continue;
                 const cdv t0 = ld(k, j);
                 st(k, j, ld(piv, j));
@@ -401,7 +435,7 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
         const int w = n - k - 1;
         bv = -1.0;
         bi = 0x7fffffff;
-        for (int idx = tid; idx < w * w; idx += HC_TB) {
+        for (int idx = tid; idx < w * w; idx += TB) {
             const int j = k + 1 + idx / w, i = k + 1 + idx % w;
             const cdv v = cdv_fnma(ld(i, j), ld(i, k), ld(k, j));
             st(i, j, v);
@@ -427,14 +461,7 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
             sh.ri[tid >> 5] = bi;
         }
         __syncthreads();
-        bv = sh.rv[0];
-        bi = sh.ri[0];
-#pragma unroll
-        for (int ww = 1; ww < HC_TW; ww++)
-            if (sh.rv[ww] > bv || (sh.rv[ww] == bv && sh.ri[ww] < bi)) {
-                bv = sh.rv[ww];
-                bi = sh.ri[ww];
-            }
+        merge_argmax<TB>(sh.rv, sh.ri, bv, bi);
     }
     *cond = 0.5 * log10(pmax / pmin);
     return HC_OK;
@@ -480,15 +507,16 @@ __device__ __forceinline__ void warp_lu64_solve(int n, const double *__restrict_
     }
 }
 
-// r_i = -h_i - sum_j J_ij dz_j in L limbs, leading limbs into RV: T threads per row (the
-// largest power of two with T n <= the block), each summing a strided part of the row,
-// then a fixed shuffle tree adds the T parts
-template <int L>
+// r_i = -h_i - sum_j J_ij dz_j in L limbs, leading limbs into RV: T = 8 threads per row,
+// each summing a strided part of the row, then a fixed shuffle tree adds the 8 parts;
+// TB / 8 rows at a time.  The order of the sums does not depend on the block size, so
+// every block size gives the same bits.
+template <int L, int TB>
 __device__ __forceinline__ void block_refine_residual(int n, const double *__restrict__ JH, const double *__restrict__ H,
                                                       const double *__restrict__ DZ, double *__restrict__ RV)
 {
-    const int T = 8 * n <= HC_TB ? 8 : 4 * n <= HC_TB ? 4 : 2 * n <= HC_TB ? 2 : 1;
-    const int g = threadIdx.x / T, q = threadIdx.x % T, rows = HC_TB / T;
+    constexpr int T = 8;
+    const int g = threadIdx.x / T, q = threadIdx.x % T, rows = TB / T;
     for (int base = 0; base < n; base += rows) {
         const int i = base + g;
         C<L> acc = c_zero<L>();
@@ -522,16 +550,16 @@ struct NewtonOut {
 // incoming z (max_i |h_i| of the leading limbs), solve J dz = -h, z += dz (all or nothing
 // on non-finite values).  Same readings as hc_newton_step.
 //
-template <int L>
+template <int L, int TB>
 __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, double t, int lu_mode, int max_refine,
                                   const Slot<L> &w, BlockShared &sh)
 {
     const int n = S.n, tid = threadIdx.x;
     NewtonOut o{0.0, 0.0, 0.0, 0.0, HC_OK, 0};
-    block_eval<L>(S, z, t, w);
+    block_eval<L, TB>(S, z, t, w);
     double r2 = 0.0;
     int fin = 1;
-    for (int i = tid; i < n; i += HC_TB) {
+    for (int i = tid; i < n; i += TB) {
         double re, im;
         ld_lead<L>(w.H, n, i, re, im);
         const double v = add_(mul_(re, re), mul_(im, im));
@@ -539,7 +567,7 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
         r2 = fmax(r2, v);
     }
     fin = block_and(fin, sh);
-    o.res = sqrt(block_max(r2, sh));
+    o.res = sqrt(block_max<TB>(r2, sh));
     if (!fin) {
         o.status = HC_NONFINITE;
         return o;
@@ -547,14 +575,14 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
     const double *D;  // the update, [2][L][n]
     bool subtract;
     if (lu_mode == HC_LU_NATIVE) {
-        o.status = block_ge<L>(n, w.JH, w.H, sh, &o.cond);
+        o.status = block_ge<L, TB>(n, w.JH, w.H, sh, &o.cond);
         if (o.status != HC_OK) return o;
         D = w.H;
         subtract = true;
     } else {
-        o.status = block_lu64<L>(n, w.JH, w.B, w.PIV, sh, &o.cond);
+        o.status = block_lu64<L, TB>(n, w.JH, w.B, w.PIV, sh, &o.cond);
         if (o.status != HC_OK) return o;
-        for (int i = tid; i < n; i += HC_TB) {
+        for (int i = tid; i < n; i += TB) {
             double re, im;
             ld_lead<L>(w.H, n, i, re, im);
             w.RV[i] = -re;
@@ -564,29 +592,29 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
         if (tid < 32) warp_lu64_solve(n, w.B, w.PIV, w.RV, w.Y);
         __syncthreads();
         double xn = 0.0;
-        for (int i = tid; i < n; i += HC_TB) {
+        for (int i = tid; i < n; i += TB) {
             st_c<L>(w.DZ, n, i, c_from<L>(w.Y[i], w.Y[n + i]));
             double re, im;
             ld_lead<L>(z, n, i, re, im);
             xn = fmax(xn, sqrt(add_(mul_(re, re), mul_(im, im))));
         }
-        xn = block_max(xn, sh);
+        xn = block_max<TB>(xn, sh);
         const double tol = ldexp(1.0, -53 * L);
         double prev = INFINITY;
         for (int it = 1; it <= max_refine; it++) {
-            block_refine_residual<L>(n, w.JH, w.H, w.DZ, w.RV);
+            block_refine_residual<L, TB>(n, w.JH, w.H, w.DZ, w.RV);
             __syncthreads();
             if (tid < 32) warp_lu64_solve(n, w.B, w.PIV, w.RV, w.Y);
             __syncthreads();
             double dn = 0.0, zz = 0.0;
-            for (int i = tid; i < n; i += HC_TB) {
+            for (int i = tid; i < n; i += TB) {
                 const double dr = w.Y[i], di = w.Y[n + i];
                 const C<L> v = c_add(ld_c<L>(w.DZ, n, i), c_from<L>(dr, di));
                 st_c<L>(w.DZ, n, i, v);
                 dn = fmax(dn, sqrt(add_(mul_(dr, dr), mul_(di, di))));
                 zz = fmax(zz, sqrt(c_abs2_lead(v)));
             }
-            block_max2(dn, zz, sh);
+            block_max2<TB>(dn, zz, sh);
             o.sweeps = it;
             if (dn <= tol * fmax(xn, zz) || dn >= prev) break;
             prev = dn;
@@ -597,7 +625,7 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
     // update, all or nothing
     int ok = 1;
     double dzn = 0.0, zn = 0.0;
-    for (int i = tid; i < n; i += HC_TB) {
+    for (int i = tid; i < n; i += TB) {
         const C<L> d = ld_c<L>(D, n, i);
         const C<L> v = subtract ? c_sub(ld_c<L>(z, n, i), d) : c_add(ld_c<L>(z, n, i), d);
         if (!c_finite_lead(v)) ok = 0;
@@ -605,14 +633,14 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
         zn = fmax(zn, sqrt(c_abs2_lead(v)));
     }
     ok = block_and(ok, sh);
-    block_max2(dzn, zn, sh);
+    block_max2<TB>(dzn, zn, sh);
     o.dzn = dzn;
     o.zn = zn;
     if (!ok) {
         o.status = HC_NONFINITE;
         return o;
     }
-    for (int i = tid; i < n; i += HC_TB) {
+    for (int i = tid; i < n; i += TB) {
         const C<L> d = ld_c<L>(D, n, i);
         st_c<L>(z, n, i, subtract ? c_sub(ld_c<L>(z, n, i), d) : c_add(ld_c<L>(z, n, i), d));
     }

@@ -44,12 +44,12 @@ __device__ __forceinline__ void proposer_features(const PathState &st, double la
 }
 
 
-// ||v||_inf from the leading limbs, the same value on every thread
-template <int L> __device__ __forceinline__ double vec_norm(int n, const double *v, BlockShared &sh)
+// ||v||_inf from the leading limbs, the same value on every thread of a TB-thread block
+template <int L, int TB> __device__ __forceinline__ double vec_norm(int n, const double *v, BlockShared &sh)
 {
     double m = 0.0;
-    for (int j = threadIdx.x; j < n; j += HC_TB) m = fmax(m, sqrt(c_abs2_lead(ld_c<L>(v, n, j))));
-    return block_max(m, sh);
+    for (int j = threadIdx.x; j < n; j += TB) m = fmax(m, sqrt(c_abs2_lead(ld_c<L>(v, n, j))));
+    return block_max<TB>(m, sh);
 }
 
 __device__ __forceinline__ void path_init(PathState &st, const hc_track_opts &o, long long pid)
@@ -78,7 +78,7 @@ __device__ __forceinline__ void path_init(PathState &st, const hc_track_opts &o,
 
 // Predictor (Alg. 3.1 "predict"; Sec. 5 for the quadratic one) at t1 = min(t + lambda, 1):
 // writes the predicted point into zh and its copy ZP; block-level, ends synchronised.
-template <int L>
+template <int L, int TB>
 __device__ void stage_predict(const hc_track_opts &o, const PathState &st, int n, const double *z,
                               const double *zp, const double *zpp, const double *tv, double *zh, double *ZP,
                               double &t1_out, double &h_out)
@@ -93,7 +93,7 @@ __device__ void stage_predict(const hc_track_opts &o, const PathState &st, int n
         // predictor (Alg. 3.1 "predict"; Sec. 5 for the quadratic one)
         if (o.predictor == HC_PRED_TANGENT && tv && st.nhist >= 2) {
             // tv[2][n] = dx/dt at the last accepted point (FP64)
-            for (int j = tid; j < n; j += HC_TB) {
+            for (int j = tid; j < n; j += TB) {
                 const C<L> v = c_add(ld_c<L>(z, n, j), c_from<L>(mul_(h, tv[j]), mul_(h, tv[n + j])));
                 st_c<L>(zh, n, j, v);
                 st_c<L>(wzp, n, j, v);
@@ -102,7 +102,7 @@ __device__ void stage_predict(const hc_track_opts &o, const PathState &st, int n
             const double w0 = __ddiv_rn(mul_(sub_(t1, st.tp), sub_(t1, st.t)), mul_(sub_(st.tpp, st.tp), sub_(st.tpp, st.t)));
             const double w1 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.t)), mul_(sub_(st.tp, st.tpp), sub_(st.tp, st.t)));
             const double w2 = __ddiv_rn(mul_(sub_(t1, st.tpp), sub_(t1, st.tp)), mul_(sub_(st.t, st.tpp), sub_(st.t, st.tp)));
-            for (int j = tid; j < n; j += HC_TB) {
+            for (int j = tid; j < n; j += TB) {
                 const C<L> v = c_add(c_add(c_mul_d(ld_c<L>(zpp, n, j), w0), c_mul_d(ld_c<L>(zp, n, j), w1)),
                                      c_mul_d(ld_c<L>(z, n, j), w2));
                 st_c<L>(zh, n, j, v);
@@ -110,14 +110,14 @@ __device__ void stage_predict(const hc_track_opts &o, const PathState &st, int n
             }
         } else if (st.nhist >= 2) {
             const double r = __ddiv_rn(h, sub_(st.t, st.tp));
-            for (int j = tid; j < n; j += HC_TB) {
+            for (int j = tid; j < n; j += TB) {
                 const C<L> zj = ld_c<L>(z, n, j);
                 const C<L> v = c_add(zj, c_mul_d(c_sub(zj, ld_c<L>(zp, n, j)), r));
                 st_c<L>(zh, n, j, v);
                 st_c<L>(wzp, n, j, v);
             }
         } else {
-            for (int j = tid; j < n; j += HC_TB) {
+            for (int j = tid; j < n; j += TB) {
                 const C<L> v = ld_c<L>(z, n, j);
                 st_c<L>(zh, n, j, v);
                 st_c<L>(wzp, n, j, v);
@@ -130,7 +130,7 @@ __device__ void stage_predict(const hc_track_opts &o, const PathState &st, int n
 // converged conv, last residual res): the divergence test, the log record, accept (shift
 // the history, grow lambda) or step back (shrink lambda), the proposer, the stop tests.
 // Block-level; st is updated identically on every thread.
-template <int L>
+template <int L, int TB>
 __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared &sh, int n, double *z,
                              double *zp, double *zpp, const double *zh, const double *ZP, double t1, double h,
                              int it, int nst, int conv, double res, double res_first, double cond,
@@ -140,7 +140,7 @@ __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared 
         st.nits += it;
         st.n_corr++;
         int ok = (nst == HC_OK) && conv;
-        const double znorm = vec_norm<L>(n, zh, sh);
+        const double znorm = vec_norm<L, TB>(n, zh, sh);
         int stop = 0;
         if (ok && !(znorm <= o.div_bound)) {
             ok = 0;
@@ -150,9 +150,9 @@ __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared 
         double pcd = -1.0;
         if (ok) {
             double m = 0.0;
-            for (int j = tid; j < n; j += HC_TB)
+            for (int j = tid; j < n; j += TB)
                 m = fmax(m, sqrt(c_abs2_lead(c_sub(ld_c<L>(zh, n, j), ld_c<L>(ZP, n, j)))));
-            pcd = block_max(m, sh);
+            pcd = block_max<TB>(m, sh);
         }
         // the log holds the stages of this call: stage n_corr is record n_corr - 1 - log0
         if (log && tid == 0 && st.n_corr - log0 <= log_cap) {
@@ -167,7 +167,7 @@ __device__ void stage_finish(const hc_track_opts &o, PathState &st, BlockShared 
             r.accepted = ok;
         }
         if (ok) {
-            for (int j = tid; j < n; j += HC_TB) {
+            for (int j = tid; j < n; j += TB) {
                 st_c<L>(zpp, n, j, ld_c<L>(zp, n, j));
                 st_c<L>(zp, n, j, ld_c<L>(z, n, j));
                 st_c<L>(z, n, j, ld_c<L>(zh, n, j));

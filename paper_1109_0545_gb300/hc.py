@@ -119,6 +119,10 @@ def load(build_if_missing: bool = True):
         L.hc_track_resume.argtypes = [ct.POINTER(vp), i, vp, vp, ct.POINTER(PathState), i,
                                       ct.POINTER(TrackOpts), ct.POINTER(PathStats), vp, i, vp]
         L.hc_track_resume.restype = i
+        L.hc_set_track_tiles.argtypes = [i, i, i, i]
+        L.hc_set_track_tiles.restype = i
+        L.hc_get_track_tiles.argtypes = [ct.POINTER(ct.c_int)] * 4
+        L.hc_get_track_tiles.restype = i
         f = ct.c_float
         L.hc_mlp_grad.argtypes = [vp, i, vp, vp, vp, f, vp, vp, vp]
         L.hc_mlp_grad.restype = i
@@ -354,6 +358,18 @@ def hc_probe_fp64_peak() -> float:
 
 def hc_set_tiles(rows_per_task: int, blocks_per_sm: int) -> None:
     _check("hc_set_tiles", load().hc_set_tiles(int(rows_per_task), int(blocks_per_sm)))
+
+
+def hc_set_track_tiles(threads_per_block: int = 0, blocks_per_sm: int = 0, factors: int = 0,
+                       grid_chunk: int = 0) -> None:
+    _check("hc_set_track_tiles", load().hc_set_track_tiles(int(threads_per_block), int(blocks_per_sm),
+                                                           int(factors), int(grid_chunk)))
+
+
+def hc_get_track_tiles() -> dict:
+    v = [ct.c_int() for _ in range(4)]
+    _check("hc_get_track_tiles", load().hc_get_track_tiles(*[ct.byref(x) for x in v]))
+    return dict(zip(("threads_per_block", "blocks_per_sm", "factors", "grid_chunk"), (x.value for x in v)))
 
 
 def hc_prof_enable(on: bool) -> None:
