@@ -684,6 +684,31 @@ def gather_stats(stats: list, dist) -> list:
     return [x for part in parts for x in part]
 
 
+def sharded_tracker(torch, hc, synth, fam, opts, dist=None, rank: int = 0, world: int = 1, L: int = 2):
+    """Paths shard in blocks over the ranks (shard_range): each rank tracks its own block
+    in one hc_track_path call on its own GPU, and the per-path statistics and end points
+    gather once, in rank order (gather_stats).  fam: list of (system, gamma).  Returns
+    (statistics of every path, end points of every path, this rank's seconds)."""
+    import numpy as np
+    lo, hi = shard_range(len(fam), rank, world)
+    mine = fam[lo:hi]
+    rows, dt = [], 0.0
+    if mine:
+        handles = [hc.system_from(sy, L, g) for sy, g in mine]
+        x0 = torch.from_numpy(hc.pack_paths([synth.limbs(np.ones(sy.n), L) for sy, _ in mine])).cuda()
+        x1 = torch.zeros_like(x0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = hc.hc_track_path(handles, x0, x1, opts)
+        dt = time.perf_counter() - t0
+        ends = hc.unpack_paths(x1.cpu().numpy(), [sy.n for sy, _ in mine], L)
+        rows = [(st, e.tolist()) for st, e in zip(stats, ends)]
+        for h in handles:
+            h.free()
+    rows = gather_stats(rows, dist)
+    return [r[0] for r in rows], [np.array(r[1]) for r in rows], dt
+
+
 def max_over_ranks(ms: float, dist, device=None) -> float:
     """The slowest rank's time (the job's time); the only collective of the bench."""
     if dist is None:
@@ -878,6 +903,19 @@ def run_gpu(args):
     e2e = {"value": npts * e2e_steps / e2e_s, "unit": "points/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    # the tracker sharded over the ranks (weak scaling: 2,432 paths of the uneven family per
+    # rank, 40 corrector stages each, FP64 LU + DD refinement; one gather of the results)
+    shard = None
+    if not args.no_extras:
+        fam = [synth.uneven_path_system(3, j) for j in range(2432 * world)]
+        sst, _, sdt = sharded_tracker(torch, hc, synth, fam,
+                                      hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, max_steps=40),
+                                      dist, rank, world)
+        sdt = max_over_ranks(sdt * 1e3, dist, "cuda") * 1e-3
+        shard = {"paths": len(fam), "paths_per_rank": 2432, "stage_cap": 40,
+                 "path_steps_per_s": sum(x["n_corr"] for x in sst) / sdt, "seconds": sdt,
+                 "gathered_paths": len(sst)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         v, cores, n, dt = oracle_points_per_s(s, pts, gamma, budget_s=15.0)
@@ -895,6 +933,7 @@ def run_gpu(args):
             "eval_tiles": tiles,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clk, "wall_s": t_wall,
+            "tracker_sharded": shard,
             "extras": compact_extras(extras),
         }
         if extras:

@@ -31,6 +31,7 @@ template <int L> struct Slot {
 struct BlockShared {
     double rv[HC_TWMAX];
     double rv2[HC_TWMAX];
+    long long rk[HC_TWMAX];
     int ri[HC_TWMAX];
     double bc[4];
     int ibc[4];
@@ -59,28 +60,56 @@ template <int TB> __device__ __forceinline__ double merge_max(const double *rv)
     return __shfl_sync(0xffffffffu, m, 0);
 }
 
-// argmax of the published (rv[w], ri[w]), ties to the lowest index
-template <int TB> __device__ __forceinline__ void merge_argmax(const double *rv, const int *ri, double &v, int &i)
+// Pivot searches compare squared moduli, which are nonnegative: the bit pattern of a
+// nonnegative double orders like its value, so the searches compare 64-bit integer keys
+// (INT pipe) instead of doubles (FP64 pipe; a block-wide argmax per column of an LU would
+// otherwise issue more FP64 comparisons than the column's elimination issues FMAs).
+// "No candidate" is key -1; a NaN modulus becomes the largest key.
+__device__ __forceinline__ long long amax_key(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b < 0 ? -1LL : b;
+}
+__device__ __forceinline__ double amax_value(long long k) { return k < 0 ? -1.0 : __longlong_as_double(k); }
+
+// (k, i) against (k2, i2): larger key, ties to the lower index
+__device__ __forceinline__ void amax_take(long long &k, int &i, long long k2, int i2)
+{
+    if (k2 > k || (k2 == k && i2 < i)) {
+        k = k2;
+        i = i2;
+    }
+}
+
+__device__ __forceinline__ void warp_argmax_key(long long &k, int &i)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        amax_take(k, i, k2, i2);
+    }
+}
+
+// argmax of the published (rk[w], ri[w]), ties to the lowest index
+template <int TB> __device__ __forceinline__ void merge_argmax_key(const long long *rk, const int *ri, long long &k, int &i)
 {
     constexpr int NW = TB / 32;
     if (NW == 1) {
-        v = rv[0];
+        k = rk[0];
         i = ri[0];
         return;
     }
     const int lane = threadIdx.x & 31;
-    v = lane < NW ? rv[lane] : -INFINITY;
+    k = lane < NW ? rk[lane] : -1LL;
     i = lane < NW ? ri[lane] : 0x7fffffff;
 #pragma unroll
     for (int o = NW / 2; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (v2 > v || (v2 == v && i2 < i)) {
-            v = v2;
-            i = i2;
-        }
+        amax_take(k, i, k2, i2);
     }
-    v = __shfl_sync(0xffffffffu, v, 0);
+    k = __shfl_sync(0xffffffffu, k, 0);
     i = __shfl_sync(0xffffffffu, i, 0);
 }
 
@@ -114,25 +143,18 @@ __device__ __forceinline__ int block_and(int v, BlockShared &sh)
     return __syncthreads_and(v);
 }
 
-// argmax of (v, i) over the block, ties to the lowest i; every thread gets the winner
-template <int TB> __device__ __forceinline__ void block_argmax(double &v, int &i, BlockShared &sh)
+// argmax of the keys (k, i) over the block, ties to the lowest i; every thread gets the
+// winner
+template <int TB> __device__ __forceinline__ void block_argmax_key(long long &k, int &i, BlockShared &sh)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (v2 > v || (v2 == v && i2 < i)) {
-            v = v2;
-            i = i2;
-        }
-    }
+    warp_argmax_key(k, i);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) {
-        sh.rv[threadIdx.x >> 5] = v;
+        sh.rk[threadIdx.x >> 5] = k;
         sh.ri[threadIdx.x >> 5] = i;
     }
     __syncthreads();
-    merge_argmax<TB>(sh.rv, sh.ri, v, i);
+    merge_argmax_key<TB>(sh.rk, sh.ri, k, i);
 }
 
 // ------------------------------------------------------------------------------ evaluation
@@ -285,6 +307,29 @@ __device__ void block_eval(const DevSys &S, const double *__restrict__ z, double
 }
 
 // ------------------------------------------------------------------------------ solves
+// The flat indices tid, tid + TB, tid + 2 TB, ... below cnt, as (idx / w, idx % w) pairs:
+// one division per walk, then an increment with a carry (the trailing updates of the
+// eliminations visit w x w entries; a division per entry is dozens of integer
+// instructions).
+struct DivWalk {
+    int hi, lo, dhi, dlo, w;
+    __device__ __forceinline__ DivWalk(int idx, int step, int w_) : w(w_)
+    {
+        hi = idx / w;
+        lo = idx - hi * w;
+        dhi = step / w;
+        dlo = step - dhi * w;
+    }
+    __device__ __forceinline__ void next()
+    {
+        hi += dhi;
+        lo += dlo;
+        if (lo >= w) {
+            lo -= w;
+            hi++;
+        }
+    }
+};
 // Elimination with partial pivoting on [A b] in the working precision (Sec. 4), block
 // version: the pivot is the entry of largest leading-limb |.|^2 (ties to the lowest row),
 // rows are swapped, the pivot's reciprocal replaces it, multipliers replace the column
@@ -297,17 +342,17 @@ __device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, B
     const size_t ap = (size_t)n * n;
     double pmax = 0.0, pmin = INFINITY;
     for (int k = 0; k < n; k++) {
-        double bv = -1.0;
+        long long bk = -1;
         int bi = 0x7fffffff;
         for (int i = k + tid; i < n; i += TB) {
-            const C<L> a = ld_c<L>(A, ap, (size_t)i * n + k);
-            const double v = c_abs2_lead(a);
-            if (v > bv) {
-                bv = v;
+            const long long key = amax_key(c_abs2_lead(ld_c<L>(A, ap, (size_t)i * n + k)));
+            if (key > bk) {
+                bk = key;
                 bi = i;
             }
         }
-        block_argmax<TB>(bv, bi, sh);
+        block_argmax_key<TB>(bk, bi, sh);
+        const double bv = amax_value(bk);
         if (!(bv > 0.0)) return HC_SINGULAR;
         pmax = fmax(pmax, bv);
         pmin = fmin(pmin, bv);
@@ -333,8 +378,9 @@ __device__ int block_ge(int n, double *__restrict__ A, double *__restrict__ b, B
         __syncthreads();
         const int w = n - k;  // columns k+1..n-1 and b
         const int cnt = (n - k - 1) * w;
-        for (int idx = tid; idx < cnt; idx += TB) {
-            const int i = k + 1 + idx / w, j = k + 1 + idx % w;
+        DivWalk dw(tid, TB, w);
+        for (int idx = tid; idx < cnt; idx += TB, dw.next()) {
+            const int i = k + 1 + dw.hi, j = k + 1 + dw.lo;
             const C<L> l = ld_c<L>(A, ap, (size_t)i * n + k);
             if (j < n)
                 st_c<L>(A, ap, (size_t)i * n + j, c_fnma(ld_c<L>(A, ap, (size_t)i * n + j), l, ld_c<L>(A, ap, (size_t)k * n + j)));
@@ -386,20 +432,21 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
     auto st = [&](int i, int j, cdv v) { B[(size_t)j * n + i] = v.re; B[ap + (size_t)j * n + i] = v.im; };
     auto mag = [&](cdv a) { return add_(mul_(a.re, a.re), mul_(a.im, a.im)); };
     // pivot of column 0
-    double bv = -1.0;
+    long long bk = -1;
     int bi = 0x7fffffff;
     for (int i = tid; i < n; i += TB) {
-        const double v = mag(ld(i, 0));
-        if (v > bv) {
-            bv = v;
+        const long long key = amax_key(mag(ld(i, 0)));
+        if (key > bk) {
+            bk = key;
             bi = i;
         }
     }
-    block_argmax<TB>(bv, bi, sh);
+    block_argmax_key<TB>(bk, bi, sh);
     double pmax = 0.0, pmin = INFINITY;
     // Two barriers per column: (A) multipliers and row swap, (B) trailing update, which also
     // finds the next column's pivot (its warps' candidates meet after the barrier)
     for (int k = 0; k < n; k++) {
+        const double bv = amax_value(bk);
         if (!(bv > 0.0)) return HC_SINGULAR;
         pmax = fmax(pmax, bv);
         pmin = fmin(pmin, bv);
@@ -433,35 +480,22 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
         // (B) the reciprocal on the diagonal, the trailing update, the next pivot
         if (tid == 0) st(k, k, inv);
         const int w = n - k - 1;
-        bv = -1.0;
+        bk = -1;
         bi = 0x7fffffff;
-        for (int idx = tid; idx < w * w; idx += TB) {
-            const int j = k + 1 + idx / w, i = k + 1 + idx % w;
+        DivWalk dw(tid, TB, w > 0 ? w : 1);
+        for (int idx = tid; idx < w * w; idx += TB, dw.next()) {
+            const int j = k + 1 + dw.hi, i = k + 1 + dw.lo;
             const cdv v = cdv_fnma(ld(i, j), ld(i, k), ld(k, j));
             st(i, j, v);
-            if (j == k + 1) {
-                const double m = mag(v);
-                if (m > bv || (m == bv && i < bi)) {
-                    bv = m;
-                    bi = i;
-                }
-            }
+            if (j == k + 1) amax_take(bk, bi, amax_key(mag(v)), i);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (v2 > bv || (v2 == bv && i2 < bi)) {
-                bv = v2;
-                bi = i2;
-            }
-        }
+        warp_argmax_key(bk, bi);
         if ((tid & 31) == 0) {
-            sh.rv[tid >> 5] = bv;
+            sh.rk[tid >> 5] = bk;
             sh.ri[tid >> 5] = bi;
         }
         __syncthreads();
-        merge_argmax<TB>(sh.rv, sh.ri, bv, bi);
+        merge_argmax_key<TB>(sh.rk, sh.ri, bk, bi);
     }
     *cond = 0.5 * log10(pmax / pmin);
     return HC_OK;

@@ -81,3 +81,41 @@ def test_paths_shard_in_blocks_and_gather_in_order():
     for r in range(world):
         assert [x["path"] for x in res[r]] == list(range(9))
         assert [x["rank"] for x in res[r]] == [0] * 5 + [1] * 4
+
+
+def _track_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_1109_0545_gb300 import hc, synth
+    torch.cuda.set_device(0)
+    fam = [synth.uneven_path_system(3, j) for j in range(11)]
+    opts = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC, max_steps=30)
+    st, ends, dt = bench.sharded_tracker(torch, hc, synth, fam, opts, dist, rank, world)
+    out[rank] = (st, [e.tolist() for e in ends])
+    dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_two_ranks_track_their_blocks_and_gather_the_single_rank_result():
+    """Two gloo ranks, each calling hc_track_path on its own block of 11 uneven-family
+    paths (both on cuda:0 here; no kernel of one rank waits on the other), gather the
+    per-path statistics and end points once: they equal, bit for bit, one rank tracking
+    all 11 paths in one call."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import bench
+    from paper_1109_0545_gb300 import hc, synth
+    fam = [synth.uneven_path_system(3, j) for j in range(11)]
+    opts = hc.hc_track_opts_default(lu_mode=hc.HC_LU_FP64_REFINE, predictor=hc.HC_PRED_QUADRATIC, max_steps=30)
+    ref_st, ref_ends, _ = bench.sharded_tracker(torch, hc, synth, fam, opts)
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_track_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        st, ends = res[r]
+        assert st == ref_st
+        assert all(np.array_equal(np.array(a), b) for a, b in zip(ends, ref_ends))
