@@ -113,8 +113,9 @@ int hc_eval_jac(hc_system *sys, int npts, double t, const double *x, double *f, 
  *   in double) at the incoming x; solve J dz = -h with partial pivoting; x += dz.
  *   lu_mode     HC_LU_NATIVE or HC_LU_FP64_REFINE
  *   max_refine  refinement sweeps for HC_LU_FP64_REFINE (>= 1); refinement stops
- *               early once ||correction||_inf <= 2^(-53 L) max(||x||_inf, ||dz||_inf)
- *               or the correction no longer shrinks (norms of the leading limbs)
+ *               early once ||correction||_inf <= 2^(-53 L) max(||x||_inf, ||dz||_inf),
+ *               or when a correction is no smaller than the previous one, which is
+ *               then not applied (norms of the leading limbs)
  *   x        device X[2][L][n][npts], updated in place where status is HC_OK
  *   res_norm device double[npts] (may be NULL)
  *   status   device int32[npts]: HC_OK, HC_SINGULAR (x unchanged) or HC_NONFINITE

@@ -803,8 +803,9 @@ int or_solve(int L, int n, const double *A, const double *b, double *x)
  *   dz_0 = LU^{-1} b_lead;  r = b - A dz;  dz += LU^{-1} r_lead;
  * Stop after max_refine sweeps, or once the correction is below 2^(-53 L) of
  * max(||x||, ||dz||) (x + dz is formed next, so that is the working precision of the
- * update), or once it no longer shrinks (the residual is at its rounding floor).
- * Returns 0/1 as ge_solve; *sweeps receives the number of refinement sweeps.
+ * update).  A correction no smaller than the previous one (the residual is at its
+ * rounding floor, or the double factors cannot reduce it) stops the refinement and is
+ * not added.  Returns 0/1 as ge_solve; *sweeps receives the number of refinement sweeps.
  */
 static int mixed_solve(int L, int n, const C *A, const C *b, C *z, int max_refine,
                        double xnorm, int *sweeps)
@@ -838,26 +839,30 @@ static int mixed_solve(int L, int n, const C *A, const C *b, C *z, int max_refin
         }
         rc = ge_solve(1, n, M, d);
         if (rc) break;
-        double dn = 0.0, zn = 0.0;
-        for (int i = 0; i < n; i++) {
-            if (it == 0) {
+        if (it == 0) {
+            for (int i = 0; i < n; i++) {
                 z[i] = c_zero();
                 z[i].re.v[0] = d[i].re.v[0];
                 z[i].im.v[0] = d[i].im.v[0];
-            } else {
-                C di = c_from(d[i].re.v[0], d[i].im.v[0]);
-                z[i] = c_add(L, z[i], di);
-                double v = sqrt(c_abs2_lead(di));
-                if (v > dn) dn = v;
             }
+            continue;
+        }
+        double dn = 0.0, zn = 0.0;
+        for (int i = 0; i < n; i++) {
+            double v = sqrt(c_abs2_lead(d[i]));
+            if (v > dn) dn = v;
+        }
+        *sweeps = it;
+        /* a correction no smaller than the previous one (the residual is at its rounding
+           floor, or the double factors cannot reduce it) ends the refinement unapplied */
+        if (dn >= prev) break;
+        for (int i = 0; i < n; i++) {
+            z[i] = c_add(L, z[i], c_from(d[i].re.v[0], d[i].im.v[0]));
             double v = sqrt(c_abs2_lead(z[i]));
             if (v > zn) zn = v;
         }
-        if (it > 0) {
-            *sweeps = it;
-            if (dn <= tol * (xnorm > zn ? xnorm : zn) || dn >= prev) break;
-            prev = dn;
-        }
+        if (dn <= tol * (xnorm > zn ? xnorm : zn)) break;
+        prev = dn;
     }
     free(M);
     free(d);

@@ -6,7 +6,7 @@
 //
 //   begin (1 block)                      init, predictor (or end-game set-up)
 //   max_it x Newton iteration (Alg. 4.1):
-//     powers (1 block)                   x_j^e
+//     powers (1 block)                   x_j^e, start-system terms
 //     monomials (grid)                   values and partials of every monomial -> V
 //     entries (grid)                     sums per Jacobian entry + homotopy -> H, J
 //     lu (1 block of 1024)               residual, FP64 LU with partial pivoting
@@ -109,21 +109,33 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
     }
 }
 
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_powers(GArgs a)
+// the power table (threads 0 .. n-1, one variable each) and the start-system terms of
+// the homotopy (threads n .. 2n-1, one row each) side by side: two dependent chains of
+// complex products per index, in parallel rather than one after the other
+#define HC_GPOW 256
+template <int L> __global__ void __launch_bounds__(HC_GPOW) k_g_powers(GArgs a)
 {
     const GStage &g = *a.g;
     if (!g_active(g)) return;
+    const int n = a.S.n;
     const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
-    for (int j = threadIdx.x; j < a.S.n; j += HC_TB) {
-        powers_of<L>(a.S, j, a.zh, a.PW);
-        homotopy_terms<L>(a.S, j, a.zh, gs, a.HS, false);
+    for (int q = threadIdx.x; q < 2 * n; q += HC_GPOW) {
+        if (q < n)
+            powers_of<L>(a.S, q, a.zh, a.PW);
+        else
+            homotopy_terms<L>(a.S, q - n, a.zh, gs, a.HS, false);
     }
 }
 
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_monomials(GArgs a)
+// one thread per monomial in one-warp blocks: all blocks are resident at once (20 or 21
+// per SM for 98,304 monomials), so every SM gets nearly the same number of monomials;
+// with 128-thread blocks 8 SMs took a sixth block while 144 had five, and the SMs that
+// finished first idled for a sixth of the kernel
+#define HC_GMONO 32
+template <int L> __global__ void __launch_bounds__(HC_GMONO) k_g_monomials(GArgs a)
 {
     if (!g_active(*a.g)) return;
-    const int q = blockIdx.x * HC_TB + threadIdx.x;
+    const int q = blockIdx.x * HC_GMONO + threadIdx.x;
     if (q < a.S.nmon) monomial_to_V<L>(a.S, __ldg(a.S.perm + q), a.zh, a.PW, a.V);
 }
 
@@ -228,7 +240,8 @@ template <int L> __global__ void __launch_bounds__(32) k_g_inverse(GArgs a, int 
 // d = INV r in FP64: 8 lanes per row, each summing the columns j = lane (mod 8) in order,
 // then a fixed shuffle tree.  first: r = -h (the first solve), dz = d; else r = the
 // residual of k_g_refine_rows, dz += d, and the refinement's stop test:
-// ||d|| <= 2^(-53 L) max(||x||, ||dz||), ||d|| no longer shrinking, or max_refine sweeps
+// ||d|| <= 2^(-53 L) max(||x||, ||dz||) or max_refine sweeps; a d no smaller than the
+// previous one ends it without being added
 #define HC_GAPPLY 1024
 template <int L> __global__ void __launch_bounds__(HC_GAPPLY, 1) k_g_apply(GArgs a, int first)
 {
@@ -250,6 +263,7 @@ template <int L> __global__ void __launch_bounds__(HC_GAPPLY, 1) k_g_apply(GArgs
     }
     __syncthreads();
     const size_t ip = (size_t)n * n;
+    __shared__ double dsh[2 * 256];  // d
     const int q = tid & 7, rows = HC_GAPPLY / 8;
     double dn = 0.0, zz = 0.0;
     for (int base = 0; base < n; base += rows) {
@@ -264,20 +278,30 @@ template <int L> __global__ void __launch_bounds__(HC_GAPPLY, 1) k_g_apply(GArgs
             d.im = add_(d.im, __shfl_xor_sync(0xffffffffu, d.im, o));
         }
         if (i < n && q == 0) {
-            const C<L> v = first ? c_from<L>(d.re, d.im) : c_add(ld_c<L>(a.DZ, n, i), c_from<L>(d.re, d.im));
-            st_c<L>(a.DZ, n, i, v);
+            dsh[i] = d.re;
+            dsh[n + i] = d.im;
             dn = fmax(dn, sqrt(add_(mul_(d.re, d.re), mul_(d.im, d.im))));
+        }
+    }
+    dn = block_max<HC_GAPPLY>(dn, sh);
+    // a refinement correction no smaller than the previous one (the residual is at its
+    // rounding floor) ends the refinement without being added
+    const bool apply = first || dn < g.prev_dn;
+    if (apply) {
+        for (int i = tid; i < n; i += HC_GAPPLY) {
+            const C<L> v = first ? c_from<L>(dsh[i], dsh[n + i]) : c_add(ld_c<L>(a.DZ, n, i), c_from<L>(dsh[i], dsh[n + i]));
+            st_c<L>(a.DZ, n, i, v);
             zz = fmax(zz, sqrt(c_abs2_lead(v)));
         }
     }
-    block_max2<HC_GAPPLY>(dn, zz, sh);
+    zz = block_max<HC_GAPPLY>(zz, sh);
     if (tid == 0) {
         if (first) {
             g.refine_active = a.o.max_refine > 0;
         } else {
             g.sweeps++;
             const double tol = ldexp(1.0, -53 * L);
-            if (dn <= tol * fmax(g.xn, zz) || dn >= g.prev_dn || g.sweeps >= a.o.max_refine) g.refine_active = 0;
+            if (!apply || dn <= tol * fmax(g.xn, zz) || g.sweeps >= a.o.max_refine) g.refine_active = 0;
             g.prev_dn = dn;
         }
     }
@@ -376,7 +400,7 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_end(GArgs a)
 template <int L>
 static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t cs, cudaGraphExec_t *exec)
 {
-    const int mblocks = (a.S.nmon + HC_TB - 1) / HC_TB;
+    const int mblocks = (a.S.nmon + HC_GMONO - 1) / HC_GMONO;
     const int eblocks = (a.S.npoly * (a.S.n + 1) + HC_TB - 1) / HC_TB;
     // the FP64 LU, and each column solve of the inverse, from shared memory when the
     // factors fit (n <= 110)
@@ -393,8 +417,8 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
     if (e != cudaSuccess) return hc_cuda_fail(e, "cudaStreamBeginCapture");
     k_g_begin<L><<<1, HC_TB, 0, cs>>>(a);
     for (int it = 0; it < max_it; it++) {
-        k_g_powers<L><<<1, HC_TB, 0, cs>>>(a);
-        k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_TB, 0, cs>>>(a);
+        k_g_powers<L><<<1, HC_GPOW, 0, cs>>>(a);
+        k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_GMONO, 0, cs>>>(a);
         k_g_chunks<L><<<(a.nchunks + HC_TB - 1) / HC_TB, HC_TB, 0, cs>>>(a);
         k_g_entries<L><<<eblocks, HC_TB, 0, cs>>>(a);
         k_g_lu<L><<<1, HC_GLU, lu_bytes, cs>>>(a, b_smem);

@@ -135,8 +135,9 @@ __device__ __forceinline__ cd cd_fnma(cd acc, cd a, cd b)  // acc - a*b
 //   dz_0 = LU^{-1} lead(-h);  repeat  r = -h - J dz (working precision),
 //   d = LU^{-1} lead(r), dz += d
 // until ||d|| <= 2^(-53 L) max(||x||, ||dz||) (the update x + dz is then exact to the
-// working precision), or ||d|| stops shrinking (the residual is at its rounding floor),
-// or max_refine sweeps.
+// working precision), or max_refine sweeps; a d no smaller than the previous one (the
+// residual is at its rounding floor, or the FP64 factors cannot reduce it) ends the
+// refinement without being added.
 template <int L>
 __global__ void __launch_bounds__(64) k_newton_mixed(int n, int npts, double *__restrict__ X,
                                                      const double *__restrict__ H,
@@ -261,15 +262,18 @@ __global__ void __launch_bounds__(64) k_newton_mixed(int n, int npts, double *__
         double dn = 0.0, zn = 0.0;
         for (int i = 0; i < n; i++) {
             const double dr = RV[HO(i)], di = RV[hplane + HO(i)];
-            const C<L> z = c_add(ld_c<L>(DZ, hplane, HO(i)), c_from<L>(dr, di));
-            st_c<L>(DZ, hplane, HO(i), z);
             const double dv = sqrt(add_(mul_(dr, dr), mul_(di, di)));
-            const double zv = sqrt(c_abs2_lead(z));
             if (dv > dn) dn = dv;
-            if (zv > zn) zn = zv;
         }
         sw = it;
-        if (dn <= tol * fmax(xn, zn) || dn >= prev) break;
+        if (dn >= prev) break;  // no longer shrinking: at the rounding floor, not applied
+        for (int i = 0; i < n; i++) {
+            const C<L> z = c_add(ld_c<L>(DZ, hplane, HO(i)), c_from<L>(RV[HO(i)], RV[hplane + HO(i)]));
+            st_c<L>(DZ, hplane, HO(i), z);
+            const double zv = sqrt(c_abs2_lead(z));
+            if (zv > zn) zn = zv;
+        }
+        if (dn <= tol * fmax(xn, zn)) break;
         prev = dn;
     }
     if (sweeps) sweeps[p] = sw;

@@ -643,14 +643,18 @@ __device__ NewtonOut block_newton(const DevSys &S, double *__restrict__ z, doubl
             double dn = 0.0, zz = 0.0;
             for (int i = tid; i < n; i += TB) {
                 const double dr = w.Y[i], di = w.Y[n + i];
-                const C<L> v = c_add(ld_c<L>(w.DZ, n, i), c_from<L>(dr, di));
-                st_c<L>(w.DZ, n, i, v);
                 dn = fmax(dn, sqrt(add_(mul_(dr, dr), mul_(di, di))));
+            }
+            dn = block_max<TB>(dn, sh);
+            o.sweeps = it;
+            if (dn >= prev) break;  // no longer shrinking: at the rounding floor, not applied
+            for (int i = tid; i < n; i += TB) {
+                const C<L> v = c_add(ld_c<L>(w.DZ, n, i), c_from<L>(w.Y[i], w.Y[n + i]));
+                st_c<L>(w.DZ, n, i, v);
                 zz = fmax(zz, sqrt(c_abs2_lead(v)));
             }
-            block_max2<TB>(dn, zz, sh);
-            o.sweeps = it;
-            if (dn <= tol * fmax(xn, zz) || dn >= prev) break;
+            zz = block_max<TB>(zz, sh);
+            if (dn <= tol * fmax(xn, zz)) break;
             prev = dn;
         }
         D = w.DZ;
