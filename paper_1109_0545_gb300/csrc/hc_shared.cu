@@ -10,7 +10,8 @@ namespace hc {
 
 // Rows r0..r1-1 of f (and J) at point p.  Every distinct monomial is evaluated for the
 // task, and the terms of rows r0..r1-1 that use it are applied (the uses of a monomial
-// are sorted by row, so they form one range, found by bisection).
+// are sorted by row, so they form one range, found by bisection).  f and J are running
+// sums in the output buffers (c_acc), renormalised once at the end (c_settle).
 template <int L, bool JAC>
 __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool live, double t, const C<L> &gs,
                                   double *__restrict__ F, double *__restrict__ J, int r0, int r1)
@@ -23,7 +24,7 @@ __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool l
         for (int i = r0; i < r1; i++) {
             C<L> fi = c_zero<L>();
             for (int q = __ldg(S.cptr + i); q < __ldg(S.cptr + i + 1); q++)
-                fi = c_add(fi, ld_c<L>(S.coef + (size_t)__ldg(S.cterm + q) * 2 * L, 1, 0));
+                fi = c_acc(fi, ld_c<L>(S.coef + (size_t)__ldg(S.cterm + q) * 2 * L, 1, 0));
             st_c<L>(F, fplane, (size_t)i * npts + p, fi);
             if (JAC)
                 for (int j = 0; j < n; j++) st_c<L>(J, jplane, ((size_t)i * n + j) * npts + p, c_zero<L>());
@@ -72,7 +73,7 @@ __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool l
             const C<L> c = ld_c<L>(S.coef + (size_t)m * 2 * L, 1, 0);
             if (!live) continue;
             const size_t fo = (size_t)i * npts + p;
-            st_c<L>(F, fplane, fo, c_add(ld_c<L>(F, fplane, fo), c_mul_nn(c, value)));
+            st_c<L>(F, fplane, fo, c_acc(ld_c<L>(F, fplane, fo), c_mul_nn(c, value)));
             if (JAC) {
                 // four entries at a time: their loads are issued together (the entries of
                 // one term are distinct, but the compiler cannot know it)
@@ -88,7 +89,7 @@ __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool l
                         }
 #pragma unroll
                     for (int q = 0; q < 4; q++)
-                        if (j0 + q < k) st_c<L>(J, jplane, o[q], c_add(acc[q], c_mul_nn(c, d[j0 + q])));
+                        if (j0 + q < k) st_c<L>(J, jplane, o[q], c_acc(acc[q], c_mul_nn(c, d[j0 + q])));
                 }
             }
         }
@@ -102,22 +103,36 @@ __device__ void eval_shared_point(const DevSys &S, const PointView<L> &V, bool l
             C<L> g = c_mul(xd1, xi);
             g.re = r_sub(g.re, r_from<L>(1.0));
             const size_t fo = (size_t)i * npts + p;
-            st_c<L>(F, fplane, fo, c_add(c_mul(gs, g), c_mul_d(ld_c<L>(F, fplane, fo), t)));
+            st_c<L>(F, fplane, fo, c_add(c_mul(gs, g), c_mul_d(c_settle(ld_c<L>(F, fplane, fo)), t)));
             if (JAC)
                 for (int j = 0; j < n; j++) {
                     const size_t o = ((size_t)i * n + j) * npts + p;
-                    C<L> v = c_mul_d(ld_c<L>(J, jplane, o), t);
+                    C<L> v = c_mul_d(c_settle(ld_c<L>(J, jplane, o)), t);
                     if (j == i) v = c_add(v, c_mul(gs, c_scale_int(xd1, dg)));
                     st_c<L>(J, jplane, o, v);
+                }
+        }
+    } else if (L == 2 && live) {
+        // f (t < 0): the running sums renormalised
+        for (int i = r0; i < r1; i++) {
+            const size_t fo = (size_t)i * npts + p;
+            st_c<L>(F, fplane, fo, c_settle(ld_c<L>(F, fplane, fo)));
+            if (JAC)
+                for (int j = 0; j < n; j++) {
+                    const size_t o = ((size_t)i * n + j) * npts + p;
+                    st_c<L>(J, jplane, o, c_settle(ld_c<L>(J, jplane, o)));
                 }
         }
     }
 }
 
 // persistent warps over tasks (32-point tile, group of rows), the row groups of a tile
-// consecutive
+// consecutive; one warp per block, so that the block scheduler deals the warps out to the
+// SMs one at a time (with four-warp blocks, 320 blocks on 152 SMs put three blocks on some
+// SMs and two on the rest, and the FP64 pipes of the latter idled for a third of the time)
+#define HC_SHARED_TB 32
 template <int L, bool JAC>
-__global__ void __launch_bounds__(128) k_eval_shared(DevSys S, int npts, double t, const double *__restrict__ X,
+__global__ void __launch_bounds__(HC_SHARED_TB) k_eval_shared(DevSys S, int npts, double t, const double *__restrict__ X,
                                                      const double *__restrict__ PW, double *__restrict__ F,
                                                      double *__restrict__ J, int rows_per_task)
 {
@@ -151,9 +166,9 @@ int launch_eval_shared(const DevSys &S, int npts, double t, const double *X, dou
     const int ntiles = (npts + 31) / 32;
     int occ = 1;
     if (J)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, true>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, true>, HC_SHARED_TB, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, false>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval_shared<L, false>, HC_SHARED_TB, 0);
     if (occ < 1) occ = 1;
     // row groups: the fewest that give two warps' tasks on every SM sub-partition (each group
     // evaluates every distinct monomial again; at 8,192 points 10 groups ran 2,560 tasks on
@@ -165,14 +180,13 @@ int launch_eval_shared(const DevSys &S, int npts, double t, const double *X, dou
     const int rpt = (int)((S.npoly + groups - 1) / groups);
     const long long tasks = (long long)ntiles * ((S.npoly + rpt - 1) / rpt);
     long long grid = (long long)sms * occ;
-    const long long need = (tasks + 3) / 4;
-    if (grid > need) grid = need;
+    if (grid > tasks) grid = tasks;
     if (grid < 1) grid = 1;
     hc_prof_mark(st, true);
     if (J)
-        k_eval_shared<L, true><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
+        k_eval_shared<L, true><<<(int)grid, HC_SHARED_TB, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
     else
-        k_eval_shared<L, false><<<(int)grid, 128, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
+        k_eval_shared<L, false><<<(int)grid, HC_SHARED_TB, 0, st>>>(S, npts, t, X, PW, F, J, rpt);
     hc_prof_mark(st, false);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return hc_cuda_fail(e, "k_eval_shared launch");

@@ -350,8 +350,8 @@ static int build_shared_tables(hc_system *s)
             const int k = vp[m + 1] - vp[m];
             if (k == 0) {
                 cterm.push_back(m);
-                ops_term += 16.0;
-                ops_shared += 16.0;
+                ops_term += 10.0;
+                ops_shared += 10.0;
                 continue;
             }
             std::vector<int32_t> key(pack + vp[m], pack + vp[m + 1]);
@@ -362,11 +362,14 @@ static int build_shared_tables(hc_system *s)
                 ops_shared += monomial_ops(pack + vp[m], k, false);
             }
             uid[m] = it->second;
-            ops_term += monomial_ops(pack + vp[m], k, true) + 16.0 * (k + 1);
-            ops_shared += 42.0 * (k + 1);
+            ops_term += monomial_ops(pack + vp[m], k, true) + 10.0 * (k + 1);
+            ops_shared += 36.0 * (k + 1);
         }
         cptr[i + 1] = (int32_t)cterm.size();
     }
+    // f_i and the Jacobian row are running sums (10 FP64 a term), renormalised once (6)
+    ops_term += 6.0 * npoly * (s->n + 1);
+    ops_shared += 6.0 * npoly * (s->n + 1);
     const int nuniq = (int)first.size();
     std::vector<int32_t> uvar_ptr((size_t)nuniq + 1, 0), uvar_pack, uuse_ptr((size_t)nuniq + 1, 0), uuse;
     for (int u = 0; u < nuniq; u++) {

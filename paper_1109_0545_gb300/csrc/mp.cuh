@@ -179,6 +179,32 @@ __device__ __forceinline__ R<4> r_add(R<4> a, R<4> b)
 
 template <int L> __device__ __forceinline__ R<L> r_sub(R<L> a, R<L> b) { return r_add(a, r_neg(b)); }
 
+// Running sums (sums read back only at their end).  Double-double: the leading limbs are
+// added by a two-sum, and its error and the lower limbs gather in the lower limb, which
+// is not renormalised: 5 FP64 instead of 8.  The lower limb may then grow past a unit in
+// the last place of the leading limb (after cancellation, past the leading limb itself);
+// r_settle renormalises the pair once, at the end (3 FP64).  Every two-sum is exact, so
+// the error of m terms is that of m rounded additions of lower limbs, a small multiple of
+// m 2^-106 of the largest partial sum.  Double and quad double accumulate with the
+// normalised addition.
+template <int L> __device__ __forceinline__ R<L> r_acc(R<L> a, R<L> b) { return r_add(a, b); }
+template <> __device__ __forceinline__ R<2> r_acc<2>(R<2> a, R<2> b)
+{
+    double s, e;
+    two_sum_ord(a.v[0], b.v[0], s, e);
+    R<2> r;
+    r.v[0] = s;
+    r.v[1] = add_(a.v[1], add_(b.v[1], e));
+    return r;
+}
+template <int L> __device__ __forceinline__ R<L> r_settle(R<L> a) { return a; }
+template <> __device__ __forceinline__ R<2> r_settle<2>(R<2> a)
+{
+    R<2> r;
+    two_sum_ord(a.v[0], a.v[1], r.v[0], r.v[1]);
+    return r;
+}
+
 // ---------------------------------------------------------------- multiplication
 __device__ __forceinline__ R<1> r_mul(R<1> a, R<1> b)  // 1 FP64
 {
@@ -318,6 +344,21 @@ template <int L> __device__ __forceinline__ C<L> c_add(C<L> a, C<L> b)
     C<L> z;
     z.re = r_add(a.re, b.re);
     z.im = r_add(a.im, b.im);
+    return z;
+}
+// running sums (r_acc): 10 FP64 in DD; c_settle renormalises at the end (6 FP64 in DD)
+template <int L> __device__ __forceinline__ C<L> c_acc(C<L> a, C<L> b)
+{
+    C<L> z;
+    z.re = r_acc<L>(a.re, b.re);
+    z.im = r_acc<L>(a.im, b.im);
+    return z;
+}
+template <int L> __device__ __forceinline__ C<L> c_settle(C<L> a)
+{
+    C<L> z;
+    z.re = r_settle<L>(a.re);
+    z.im = r_settle<L>(a.im);
     return z;
 }
 template <int L> __device__ __forceinline__ C<L> c_sub(C<L> a, C<L> b)

@@ -263,7 +263,8 @@ __device__ __forceinline__ void entry_finish(const DevSys &S, int e, double t, C
         st_c<L>(JH, (size_t)n * n, (size_t)i * n + j, acc);
 }
 
-// The contributions r0 .. r1-1 of the transpose table summed in order
+// The contributions r0 .. r1-1 of the transpose table summed in order (a running sum,
+// renormalised at the end)
 template <int L>
 __device__ __forceinline__ C<L> sum_contributions(const DevSys &S, int r0, int r1, const double *__restrict__ V)
 {
@@ -272,8 +273,8 @@ __device__ __forceinline__ C<L> sum_contributions(const DevSys &S, int r0, int r
     // unrolled so that the gathers of several contributions are in flight together; the
     // additions keep their order
 #pragma unroll 4
-    for (int r = r0; r < r1; r++) acc = c_add(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
-    return acc;
+    for (int r = r0; r < r1; r++) acc = c_acc(acc, ld_c<L>(V, vplane, __ldg(S.tlist + r)));
+    return c_settle(acc);
 }
 
 // Phase 2 for one entry e: the sum of its contributions in the original monomial order,

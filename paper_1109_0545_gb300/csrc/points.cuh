@@ -50,9 +50,9 @@ template <int L> __device__ __forceinline__ C<L> gamma_one_minus_t(double gre, d
 // the 3k-6 + k + 1 of the paper plus its k+1 coefficient products.  Then
 // Coefficient_Product (Alg. 4.1) reduces to f_i += value, J_{i,ij} += a_j D_j.
 // J is accumulated in place in the output buffer (this lane is its only writer).
-// Products inside the chain stay unnormalised (c_mul_nn); every addition renormalises,
-// and a pre[] entry with k == 1 (the common factor alone) also reaches J only through an
-// addition, so every stored value is normalised.
+// Products inside the chain stay unnormalised (c_mul_nn).  f_i and the J row are running
+// sums (c_acc, not renormalised in double-double), renormalised once when the row is
+// complete (c_settle), so every value stored at the end is normalised.
 //
 template <int L, bool JAC>
 __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool live, double t,
@@ -73,7 +73,7 @@ __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool liv
             const int q0 = __ldg(S.var_ptr + m), k = __ldg(S.var_ptr + m + 1) - q0;
             C<L> c = ld_c<L>(S.coef + (size_t)m * 2 * L, 1, 0);
             if (k == 0) {
-                fi = c_add(fi, c);
+                fi = c_acc(fi, c);
                 continue;
             }
             // common factor with the coefficient folded in
@@ -85,7 +85,7 @@ __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool liv
             }
             if (!JAC) {
                 for (int j = 0; j < k; j++) cf = c_mul_nn(cf, V.x(__ldg(S.var_pack + q0 + j) & 0xffff));
-                fi = c_add(fi, cf);
+                fi = c_acc(fi, cf);
                 continue;
             }
             // prefix products
@@ -93,11 +93,11 @@ __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool liv
             for (int j = 1; j < k; j++) pre[j] = c_mul_nn(pre[j - 1], V.x(__ldg(S.var_pack + q0 + j - 1) & 0xffff));
             const int pk_last = __ldg(S.var_pack + q0 + k - 1);
             const C<L> xl = V.x(pk_last & 0xffff);
-            fi = c_add(fi, c_mul_nn(pre[k - 1], xl));
+            fi = c_acc(fi, c_mul_nn(pre[k - 1], xl));
             // backward sweep: D_j = pre_j * suf_j
             if (live) {
                 const size_t o = jrow + (size_t)(pk_last & 0xffff) * npts;
-                st_c<L>(J, jplane, o, c_add(ld_c<L>(J, jplane, o), c_scale_int(pre[k - 1], pk_last >> 16)));
+                st_c<L>(J, jplane, o, c_acc(ld_c<L>(J, jplane, o), c_scale_int(pre[k - 1], pk_last >> 16)));
             }
             C<L> suf = xl;
             for (int j = k - 2; j >= 0; j--) {
@@ -105,11 +105,12 @@ __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool liv
                 const C<L> d = c_scale_int(c_mul_nn(pre[j], suf), pk >> 16);
                 if (live) {
                     const size_t o = jrow + (size_t)(pk & 0xffff) * npts;
-                    st_c<L>(J, jplane, o, c_add(ld_c<L>(J, jplane, o), d));
+                    st_c<L>(J, jplane, o, c_acc(ld_c<L>(J, jplane, o), d));
                 }
                 if (j > 0) suf = c_mul_nn(suf, V.x(pk & 0xffff));
             }
         }
+        fi = c_settle(fi);
         if (t >= 0.0) {
             // homotopy assembly: h_i = gamma (1-t) (x_i^d - 1) + t f_i,
             // dh_i/dx_j = t J_ij + [i == j] gamma (1-t) d x_i^(d-1)
@@ -122,10 +123,15 @@ __device__ void eval_rows_point(const DevSys &S, const PointView<L> &V, bool liv
             if (JAC && live) {
                 for (int j = 0; j < n; j++) {
                     const size_t o = jrow + (size_t)j * npts;
-                    C<L> v = c_mul_d(ld_c<L>(J, jplane, o), t);
+                    C<L> v = c_mul_d(c_settle(ld_c<L>(J, jplane, o)), t);
                     if (j == i) v = c_add(v, c_mul(gs, c_scale_int(xd1, d)));
                     st_c<L>(J, jplane, o, v);
                 }
+            }
+        } else if (L == 2 && JAC && live) {
+            for (int j = 0; j < n; j++) {
+                const size_t o = jrow + (size_t)j * npts;
+                st_c<L>(J, jplane, o, c_settle(ld_c<L>(J, jplane, o)));
             }
         }
         if (live) st_c<L>(F, fplane, (size_t)i * npts + p, fi);

@@ -16,6 +16,8 @@ C_MUL = {1: 4, 2: 32, 4: 2 * 141}      # normalised complex product
 C_MUL_NN = {1: 4, 2: 26, 4: 2 * 141}   # product feeding a product or a sum
 C_ADD = {1: 2, 2: 16, 4: 2 * 47}
 R_ADD = {1: 1, 2: 8, 4: 47}
+C_ACC = {1: 2, 2: 10, 4: 2 * 47}       # a term of a running sum (c_acc)
+C_SETTLE = {1: 0, 2: 6, 4: 0}          # the running sum renormalised at its end
 C_MUL_D = {1: 2, 2: 12, 4: 2 * 40}
 
 
@@ -36,7 +38,7 @@ def pow_mults(e: int) -> int:
 
 def eval_ops_per_point(s, L: int, homotopy: bool = True, jac: bool = True) -> int:
     """FP64 instructions of the evaluation kernel for one point of system ``s``."""
-    cm, cn, ca = C_MUL[L], C_MUL_NN[L], C_ADD[L]
+    cm, cn, ca = C_MUL[L], C_MUL_NN[L], C_ACC[L]
     total = 0
     vp, ve = s.var_ptr, s.var_exp
     for m in range(s.nmon):
@@ -51,6 +53,8 @@ def eval_ops_per_point(s, L: int, homotopy: bool = True, jac: bool = True) -> in
             continue
         nmul = n2 + (3 * k - 3 if k >= 2 else 1)
         total += nmul * cn + (k + 1) * ca + sum(scale_int(L, int(a)) for a in ex)
+    # f_i and the row of J are running sums, renormalised once per row
+    total += s.npoly * (1 + (s.n if jac else 0)) * C_SETTLE[L]
     if homotopy:
         deg = np.zeros(s.npoly, dtype=np.int64)
         for i in range(s.npoly):
@@ -58,9 +62,9 @@ def eval_ops_per_point(s, L: int, homotopy: bool = True, jac: bool = True) -> in
                 deg[i] = max(deg[i], int(ve[vp[m]:vp[m + 1]].sum()))
         for i in range(s.npoly):
             d = int(deg[i])
-            row = (pow_mults(d - 1) + 2) * cm + R_ADD[L] + C_MUL_D[L] + ca
+            row = (pow_mults(d - 1) + 2) * cm + R_ADD[L] + C_MUL_D[L] + C_ADD[L]
             if jac:
-                row += s.n * C_MUL_D[L] + scale_int(L, d) + cm + ca
+                row += s.n * C_MUL_D[L] + scale_int(L, d) + cm + C_ADD[L]
             total += row
     return total
 

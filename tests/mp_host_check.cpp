@@ -1,7 +1,7 @@
 // Host build of the library's multi-limb arithmetic (csrc/mp.cuh, compiled here with
 // shims that map the device rounding intrinsics to the identical IEEE operations of the
-// host) on adversarial operands: heavy cancellation in additions, products, complex dot
-// products.  Prints operands and results as hex floats for an exact check in Python.
+// host) on adversarial operands: heavy cancellation in additions, products, running
+// sums.  Prints operands and results as hex floats for an exact check in Python.
 #include <cstdio>
 #include <cstdlib>
 #include <random>
@@ -38,9 +38,23 @@ template <int L> static void run(int mode, int count)
             for (int k = 1; k < L; k++) b.v[k] = -a.v[k] * (1 + urand() * 0x1p-30);
             b.v[1] += u;
             r = r_add(a, b);
-        } else {                  // a * b
+        } else if (mode == 2) {   // a * b
             b = rand_r<L>(std::ldexp(1.0, (int)(rng() % 40) - 20));
             r = r_mul(a, b);
+        } else {                  // a running sum of m terms (r_acc, r_settle), mixed scales
+            const int m = 2 + (int)(rng() % 300);
+            printf("%d ", m);
+            R<L> acc = r_zero<L>();
+            for (int q = 0; q < m; q++) {
+                R<L> t = rand_r<L>(std::ldexp(1.0, (int)(rng() % 24) - 12));
+                if (q > 0 && rng() % 4 == 0) t = r_neg(acc);  // cancel the sum so far
+                if (q > 0 && rng() % 7 == 0) t = r_add(r_neg(acc), rand_r<L>(0x1p-60));
+                acc = r_acc<L>(acc, t);
+                out(t);
+            }
+            out(r_settle<L>(acc));
+            printf("\n");
+            continue;
         }
         out(a); out(b); out(r); printf("\n");
     }

@@ -89,3 +89,26 @@ def test_host_build_of_the_device_arithmetic(checker, L, mode):
             unsep += 1
     assert worst <= bound, worst
     assert unsep == 0
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_running_sums_within_bound_and_settled(checker, L):
+    """r_acc over m terms (some of them cancelling the sum so far, exactly or up to a
+    small remainder), then r_settle: the error is within m 2^(-52 L + 2) of the largest
+    partial sum, and the settled result is normalised."""
+    out = subprocess.run([checker, str(L), "3", "400"], capture_output=True, text=True, check=True).stdout
+    worst = 0.0
+    for line in out.splitlines():
+        tok = line.split()
+        m = int(tok[0])
+        v = [float.fromhex(t) for t in tok[1:]]
+        assert len(v) == (m + 1) * L
+        total, biggest = Fr(0), Fr(0)
+        for q in range(m):
+            total += sum(Fr(x) for x in v[q * L:(q + 1) * L])
+            biggest = max(biggest, abs(total))
+        r = v[m * L:]
+        if biggest:
+            worst = max(worst, abs(float((sum(Fr(x) for x in r) - total) / biggest)) / m)
+        assert _separated(r), r
+    assert worst <= 2.0 ** (-52 * L + 2), worst
