@@ -815,6 +815,13 @@ def run_gpu(args):
     if roofline["traffic"] and eval_avg_ms > 0:
         # the secondary counter: DRAM bytes per second of the evaluation kernel (the HBM is idle)
         roofline["hbm_gbs"] = roofline["traffic"] / (eval_avg_ms * 1e-3) / 1e9
+    # against the FP64 issue rate the profiler states as the peak (2 FP64 thread
+    # instructions per clock per SM) at the median SM clock of the timed region
+    mhz = clk.get("sm_mhz") if isinstance(clk, dict) else None
+    if mhz:
+        nominal = 2.0 * torch.cuda.get_device_properties(local).multi_processor_count * mhz * 1e6 / 1e9
+        roofline["nominal_peak"] = nominal
+        roofline["frac_of_nominal"] = achieved / nominal
 
     extras = {}
     # the secondary measurements are single-GPU figures: with several ranks they would hold

@@ -6,10 +6,11 @@
 //
 //   begin (1 block)                      init, predictor (or end-game set-up)
 //   max_it x Newton iteration (Alg. 4.1):
-//     powers (1 block)                   x_j^e, start-system terms
+//     powers (2n blocks of 1 thread)     x_j^e, start-system terms
 //     monomials (grid)                   values and partials of every monomial -> V
 //     entries (grid)                     sums per Jacobian entry + homotopy -> H, J
-//     lu (1 block of 1024)               residual, FP64 LU with partial pivoting
+//     lu prep (1 block of 1024)          residual, leading limbs of J
+//     ceil(n / 16) x [panel (1 block), update (grid)]   FP64 LU with partial pivoting
 //     inverse (n warps)                  the FP64 inverse, one column per warp
 //     apply (1 block)                    dz_0 = inverse x (-h)
 //     max_refine x [residual rows (n warps), apply (1 block)]   refinement in L limbs
@@ -39,6 +40,7 @@ namespace hc {
 
 struct GStage {
     double t1, h, res, res_first, cond, dzn, zn, xn, prev_dn;
+    double pmax, pmin;        // the blocked LU's largest and smallest pivot so far
     int it, conv, nst, allowed, refine_active, sweeps, pad[2];
 };
 
@@ -50,6 +52,7 @@ struct GArgs {
     double *z, *zp, *zpp, *zh, *ZP, *PW, *V, *HS, *H, *JH, *B, *RV, *DZ;
     double *INV;              // [2][n][n] the inverse of the FP64 factors, column-major
     int32_t *PIV;
+    int32_t *PSTEP;           // [n] the blocked LU's pivot row of each step
     // the entries' contribution lists cut into chunks of at most `chunk`, summed in
     // parallel (k_g_chunks), then per entry in chunk order (k_g_entries)
     const int32_t *cbeg;      // [nchunks+1] chunk c covers tlist[cbeg[c] .. cend[c])
@@ -109,21 +112,22 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
     }
 }
 
-// the power table (threads 0 .. n-1, one variable each) and the start-system terms of
-// the homotopy (threads n .. 2n-1, one row each) side by side: two dependent chains of
-// complex products per index, in parallel rather than one after the other
-#define HC_GPOW 256
-template <int L> __global__ void __launch_bounds__(HC_GPOW) k_g_powers(GArgs a)
+// the start-system terms of the homotopy (blocks 0 .. n-1, one row each) and the power
+// table (blocks n .. 2n-1, one variable each): one dependent chain of complex products
+// per index, each in a block of its own so that the chains spread over the SMs (one
+// SM's FP64 pipe completes two lanes' instructions per clock; in one block of 256
+// threads they took 0.17 ms per Newton iteration at n = 96 in quad double).  The long
+// chains (x_i^(d-1) by binary powering) come first, so they start first.
+template <int L> __global__ void __launch_bounds__(1) k_g_powers(GArgs a)
 {
     const GStage &g = *a.g;
     if (!g_active(g)) return;
-    const int n = a.S.n;
-    const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
-    for (int q = threadIdx.x; q < 2 * n; q += HC_GPOW) {
-        if (q < n)
-            powers_of<L>(a.S, q, a.zh, a.PW);
-        else
-            homotopy_terms<L>(a.S, q - n, a.zh, gs, a.HS, false);
+    const int n = a.S.n, q = blockIdx.x;
+    if (q < n) {
+        const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
+        homotopy_terms<L>(a.S, q, a.zh, gs, a.HS, false);
+    } else {
+        powers_of<L>(a.S, q - n, a.zh, a.PW);
     }
 }
 
@@ -164,20 +168,17 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_entries(GArgs a)
     entry_finish<L>(a.S, e, g.t1, acc, a.HS, a.H, a.JH, nullptr);
 }
 
-#define HC_GLU 1024  // threads of the whole-GPU engine's LU block
+#define HC_GLU 1024  // threads of the whole-GPU engine's LU blocks
 
-// residual of the incoming point and the FP64 LU (block_newton's first part), by one block
-// of 1024 threads: the trailing updates keep all of one SM's warps busy
-template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu(GArgs a, int b_smem)
+// The residual ||h|| and ||x|| of the incoming point (leading limbs), every thread
+// getting them; returns 0 if h is not finite
+template <int L> __device__ __forceinline__ int g_residual(const GArgs &a, BlockShared &sh, double &res, double &xn)
 {
-    __shared__ BlockShared sh;
-    extern __shared__ double fsh[];  // (b_smem) the factors [2][n][n]
-    GStage &g = *a.g;
-    if (!g_active(g)) return;
-    const int n = a.S.n, tid = threadIdx.x;
-    double r2 = 0.0, xn = 0.0;
+    const int n = a.S.n;
+    double r2 = 0.0;
+    xn = 0.0;
     int fin = 1;
-    for (int i = tid; i < n; i += HC_GLU) {
+    for (int i = threadIdx.x; i < n; i += HC_GLU) {
         double re, im;
         ld_lead<L>(a.H, n, i, re, im);
         const double v = add_(mul_(re, re), mul_(im, im));
@@ -188,7 +189,22 @@ template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu(GArgs a, in
     }
     fin = block_and(fin, sh);
     block_max2<HC_GLU>(r2, xn, sh);
-    const double res = sqrt(r2);
+    res = sqrt(r2);
+    return fin;
+}
+
+// residual of the incoming point and the FP64 LU (block_newton's first part), by one block
+// of 1024 threads: the trailing updates keep all of one SM's warps busy.  For systems too
+// large for the blocked LU's panels in shared memory.
+template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu(GArgs a, int b_smem)
+{
+    __shared__ BlockShared sh;
+    extern __shared__ double fsh[];  // (b_smem) the factors [2][n][n]
+    GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int n = a.S.n, tid = threadIdx.x;
+    double res, xn;
+    const int fin = g_residual<L>(a, sh, res, xn);
     double cond = 0.0;
     double *Bf = b_smem ? fsh : a.B;
     const int status = fin ? block_lu64<L, HC_GLU>(n, a.JH, Bf, a.PIV, sh, &cond) : HC_NONFINITE;
@@ -212,9 +228,204 @@ template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu(GArgs a, in
     }
 }
 
+// ---- The blocked FP64 LU: the same factors, pivots and condition estimate as
+// block_lu64, bit for bit, in panels of HC_GLU_NB columns spread over the GPU.  A single
+// block's LU is bound by one SM's FP64 pipe (two lanes a clock: 0.57 ms at n = 96), while
+// its trailing updates are independent per column.  Per panel:
+//   k_g_panel (1 block)     the panel's columns factored in shared memory: pivot search,
+//                           row swap (within the panel), multipliers, rank-1 updates
+//   k_g_lu_update (grid)    every other column: the panel's row swaps, then the panel's
+//                           eliminations in step order (forward substitution with the unit
+//                           lower triangle and the update of the rows below, one sweep)
+// Every entry receives the same operations in the same order as in block_lu64 (the
+// updates a_ij -= l_ik a_kj by increasing k, the swaps by increasing step), so the results
+// are identical.
+#define HC_GLU_NB 16
+#define HC_GPANEL 256
+#define HC_GUPD 4   // columns (warps) per block of k_g_lu_update
+
+// residual, norms, the leading limbs of J into B (column-major), the identity permutation
+template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu_prep(GArgs a)
+{
+    __shared__ BlockShared sh;
+    GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int n = a.S.n, tid = threadIdx.x;
+    double res, xn;
+    const int fin = g_residual<L>(a, sh, res, xn);
+    const size_t ap = (size_t)n * n;
+    if (fin) {
+        for (int q = tid; q < n * n; q += HC_GLU) {
+            const int j = q / n, i = q - j * n;
+            double re, im;
+            ld_lead<L>(a.JH, ap, (size_t)i * n + j, re, im);
+            a.B[q] = re;
+            a.B[ap + q] = im;
+        }
+        for (int q = tid; q < n; q += HC_GLU) a.PIV[q] = q;
+    }
+    if (tid == 0) {
+        g.res = res;
+        if (g.res_first < 0) g.res_first = res;
+        g.cond = 0.0;
+        g.xn = xn;
+        g.pmax = 0.0;
+        g.pmin = INFINITY;
+        g.refine_active = 0;
+        g.prev_dn = INFINITY;
+        g.sweeps = 0;
+        if (!fin) {
+            g.it++;
+            g.nst = HC_NONFINITE;
+        }
+    }
+}
+
+// columns kb .. kb+nb-1, rows kb .. n-1 (m rows), factored in shared memory
+template <int L> __global__ void __launch_bounds__(HC_GPANEL) k_g_panel(GArgs a, int kb)
+{
+    __shared__ BlockShared sh;
+    extern __shared__ double psh[];  // [2][nb][m], column-major
+    GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int n = a.S.n, tid = threadIdx.x, m = n - kb, nb = min(HC_GLU_NB, m);
+    const size_t ap = (size_t)n * n, pp = (size_t)nb * m;
+    for (int q = tid; q < nb * m; q += HC_GPANEL) {
+        const int c = q / m, r = q - c * m;
+        const size_t o = (size_t)(kb + c) * n + kb + r;
+        psh[q] = a.B[o];
+        psh[pp + q] = a.B[ap + o];
+    }
+    __syncthreads();
+    auto ld = [&](int i, int c) { return cdv{psh[(size_t)c * m + i], psh[pp + (size_t)c * m + i]}; };
+    auto st = [&](int i, int c, cdv v) { psh[(size_t)c * m + i] = v.re; psh[pp + (size_t)c * m + i] = v.im; };
+    auto mag = [&](cdv v) { return add_(mul_(v.re, v.re), mul_(v.im, v.im)); };
+    double pmax = g.pmax, pmin = g.pmin;
+    for (int c = 0; c < nb; c++) {
+        // pivot: the largest squared modulus in column c, rows c .. m-1, ties to the lowest
+        long long bk = -1;
+        int bi = 0x7fffffff;
+        for (int i = c + tid; i < m; i += HC_GPANEL) amax_take(bk, bi, amax_key(mag(ld(i, c))), i);
+        block_argmax_key<HC_GPANEL>(bk, bi, sh);
+        const double bv = amax_value(bk);
+        if (!(bv > 0.0)) {
+            if (tid == 0) {
+                g.it++;
+                g.nst = HC_SINGULAR;
+            }
+            return;
+        }
+        pmax = fmax(pmax, bv);
+        pmin = fmin(pmin, bv);
+        const int piv = bi;
+        if (piv != c)
+            for (int cc = tid; cc < nb; cc += HC_GPANEL) {
+                const cdv t0 = ld(c, cc);
+                st(c, cc, ld(piv, cc));
+                st(piv, cc, t0);
+            }
+        if (tid == 0) {
+            a.PSTEP[kb + c] = kb + piv;
+            if (piv != c) {
+                const int t0 = a.PIV[kb + c];
+                a.PIV[kb + c] = a.PIV[kb + piv];
+                a.PIV[kb + piv] = t0;
+            }
+        }
+        __syncthreads();
+        // the multipliers of column c and the pivot's reciprocal conj(a) / |a|^2 on the
+        // diagonal (formed only by the threads that use it)
+        cdv inv = {0.0, 0.0};
+        if (tid == 0 || c + 1 + tid < m) {
+            const cdv av = ld(c, c);
+            const double r = 1.0 / bv;
+            inv = {av.re * r, -av.im * r};
+        }
+        for (int i = c + 1 + tid; i < m; i += HC_GPANEL) st(i, c, cdv_mul(ld(i, c), inv));
+        __syncthreads();
+        if (tid == 0) st(c, c, inv);
+        // the rank-1 update of the panel's columns c+1 .. nb-1
+        const int w = m - c - 1, wc = nb - c - 1;
+        for (int idx = tid; idx < w * wc; idx += HC_GPANEL) {
+            const int cj = c + 1 + idx / w, i = c + 1 + idx % w;
+            st(i, cj, cdv_fnma(ld(i, cj), ld(i, c), ld(c, cj)));
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < nb * m; q += HC_GPANEL) {
+        const int c = q / m, r = q - c * m;
+        const size_t o = (size_t)(kb + c) * n + kb + r;
+        a.B[o] = psh[q];
+        a.B[ap + o] = psh[pp + q];
+    }
+    if (tid == 0) {
+        g.pmax = pmax;
+        g.pmin = pmin;
+        if (kb + nb == n) g.cond = 0.5 * log10(pmax / pmin);
+    }
+}
+
+// every column outside the panel kb .. kb+nb-1, one warp each: rows kb .. n-1 of the
+// column in shared memory, the panel's swaps, and (columns right of the panel) the
+// panel's eliminations, with the panel's multipliers from a shared-memory copy
+template <int L> __global__ void __launch_bounds__(32 * HC_GUPD) k_g_lu_update(GArgs a, int kb)
+{
+    extern __shared__ double ush[];  // multipliers [2][nb][m], then per warp a column [2][m]
+    const GStage &g = *a.g;
+    if (!g_active(g)) return;
+    const int n = a.S.n, m = n - kb, nb = min(HC_GLU_NB, m), lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const size_t ap = (size_t)n * n, pp = (size_t)nb * m;
+    int j = blockIdx.x * HC_GUPD + wid;
+    if (j >= kb) j += nb;
+    double *lm = ush, *col = ush + 2 * pp + (size_t)wid * 2 * m;
+    for (int q = threadIdx.x; q < nb * m; q += 32 * HC_GUPD) {
+        const int c = q / m, r = q - c * m;
+        const size_t o = (size_t)(kb + c) * n + kb + r;
+        lm[q] = a.B[o];
+        lm[pp + q] = a.B[ap + o];
+    }
+    __syncthreads();
+    if (j >= n) return;
+    const size_t co = (size_t)j * n + kb;
+    for (int i = lane; i < m; i += 32) {
+        col[i] = a.B[co + i];
+        col[m + i] = a.B[ap + co + i];
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int c = 0; c < nb; c++) {
+            const int p = a.PSTEP[kb + c] - kb;
+            if (p != c) {
+                const double tr = col[c], ti = col[m + c];
+                col[c] = col[p];
+                col[m + c] = col[m + p];
+                col[p] = tr;
+                col[m + p] = ti;
+            }
+        }
+    __syncwarp();
+    if (j > kb)
+        for (int c = 0; c < nb; c++) {
+            const cdv u = {col[c], col[m + c]};
+            for (int i = c + 1 + lane; i < m; i += 32) {
+                const cdv v = cdv_fnma(cdv{col[i], col[m + i]}, cdv{lm[(size_t)c * m + i], lm[pp + (size_t)c * m + i]}, u);
+                col[i] = v.re;
+                col[m + i] = v.im;
+            }
+            __syncwarp();
+        }
+    for (int i = lane; i < m; i += 32) {
+        a.B[co + i] = col[i];
+        a.B[ap + co + i] = col[m + i];
+    }
+}
+
 // column j = blockIdx.x of the inverse of the FP64 factors: the solve of e_j by one warp
-// (warp_lu64_solve), from a shared-memory copy of the factors when they fit
-template <int L> __global__ void __launch_bounds__(32) k_g_inverse(GArgs a, int b_smem)
+// (warp_lu64_solve), from a shared-memory copy of the factors when they fit.  The block's
+// other warps only help with that copy (2 n^2 doubles from L2: 576 loads per lane for
+// one warp alone at n = 96).
+#define HC_GINV 256
+template <int L> __global__ void __launch_bounds__(HC_GINV) k_g_inverse(GArgs a, int b_smem)
 {
     extern __shared__ double ish[];  // e_j [2][n], y [2][n], then (b_smem) the factors
     const GStage &g = *a.g;
@@ -224,9 +435,11 @@ template <int L> __global__ void __launch_bounds__(32) k_g_inverse(GArgs a, int 
     const double *Bf = a.B;
     if (b_smem) {
         double *Bs = ish + 4 * n;
-        for (int q = lane; q < 2 * n * n; q += 32) Bs[q] = a.B[q];
+        for (int q = threadIdx.x; q < 2 * n * n; q += HC_GINV) Bs[q] = a.B[q];
         Bf = Bs;
     }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
     for (int q = lane; q < 2 * n; q += 32) ej[q] = q == j ? 1.0 : 0.0;
     __syncwarp();
     warp_lu64_solve(n, Bf, a.PIV, ej, y);
@@ -408,21 +621,40 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
     const size_t vec4 = sizeof(double) * 4 * (size_t)a.S.n;
     const int b_smem = vec4 + bsm <= 200 * 1024;
     const size_t lu_bytes = b_smem ? bsm : 0, inv_bytes = vec4 + (b_smem ? bsm : 0);
+    // the blocked LU while a panel and the update kernel's copies fit in shared memory
+    const int n = a.S.n, nb0 = n < HC_GLU_NB ? n : HC_GLU_NB;
+    auto panel_bytes = [&](int m, int nb) { return sizeof(double) * 2 * (size_t)nb * m; };
+    auto upd_bytes = [&](int m, int nb) { return sizeof(double) * 2 * (size_t)m * (nb + HC_GUPD); };
+    const bool blocked = upd_bytes(n, nb0) <= 200 * 1024;
     cudaError_t ea = cudaFuncSetAttribute(k_g_lu<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(lu_bytes > 0 ? lu_bytes : 1));
     if (ea == cudaSuccess)
         ea = cudaFuncSetAttribute(k_g_inverse<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_bytes);
+    if (ea == cudaSuccess && blocked)
+        ea = cudaFuncSetAttribute(k_g_panel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_bytes(n, nb0));
+    if (ea == cudaSuccess && blocked)
+        ea = cudaFuncSetAttribute(k_g_lu_update<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_bytes(n, nb0));
     if (ea != cudaSuccess) return hc_cuda_fail(ea, "whole-GPU engine shared memory");
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return hc_cuda_fail(e, "cudaStreamBeginCapture");
     k_g_begin<L><<<1, HC_TB, 0, cs>>>(a);
     for (int it = 0; it < max_it; it++) {
-        k_g_powers<L><<<1, HC_GPOW, 0, cs>>>(a);
+        k_g_powers<L><<<2 * a.S.n, 1, 0, cs>>>(a);
         k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_GMONO, 0, cs>>>(a);
         k_g_chunks<L><<<(a.nchunks + HC_TB - 1) / HC_TB, HC_TB, 0, cs>>>(a);
         k_g_entries<L><<<eblocks, HC_TB, 0, cs>>>(a);
-        k_g_lu<L><<<1, HC_GLU, lu_bytes, cs>>>(a, b_smem);
-        k_g_inverse<L><<<a.S.n, 32, inv_bytes, cs>>>(a, b_smem);
+        if (blocked) {
+            k_g_lu_prep<L><<<1, HC_GLU, 0, cs>>>(a);
+            for (int kb = 0; kb < n; kb += HC_GLU_NB) {
+                const int m = n - kb, nb = m < HC_GLU_NB ? m : HC_GLU_NB, others = n - nb;
+                k_g_panel<L><<<1, HC_GPANEL, panel_bytes(m, nb), cs>>>(a, kb);
+                if (others > 0)
+                    k_g_lu_update<L><<<(others + HC_GUPD - 1) / HC_GUPD, 32 * HC_GUPD, upd_bytes(m, nb), cs>>>(a, kb);
+            }
+        } else {
+            k_g_lu<L><<<1, HC_GLU, lu_bytes, cs>>>(a, b_smem);
+        }
+        k_g_inverse<L><<<a.S.n, HC_GINV, inv_bytes, cs>>>(a, b_smem);
         k_g_apply<L><<<1, HC_GAPPLY, 0, cs>>>(a, 1);
         for (int r = 0; r < max_refine; r++) {
             k_g_refine_rows<L><<<a.S.n, 32, 0, cs>>>(a);
@@ -463,7 +695,8 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     const size_t o_v = put(sizeof(double) * 2 * L * (vplane > 0 ? vplane : 1));
     const size_t o_hs = put(3 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n),
                  o_inv = put(sizeof(double) * 2 * (size_t)n * n);
-    const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n);
+    const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n),
+                 o_pstep = put(sizeof(int32_t) * n);
     // chunks of the entries' contribution lists (from the transpose table's offsets)
     const int ne = s->npoly * (n + 1);
     std::vector<int32_t> tptr((size_t)ne + 1), cbeg, cend, eptr((size_t)ne + 1, 0);
@@ -504,6 +737,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     a.RV = (double *)(b + o_rv);
     a.DZ = (double *)(b + o_dz);
     a.PIV = (int32_t *)(b + o_piv);
+    a.PSTEP = (int32_t *)(b + o_pstep);
     a.cbeg = (const int32_t *)(b + o_cb);
     a.cend = (const int32_t *)(b + o_ce);
     a.eptr = (const int32_t *)(b + o_ep);

@@ -108,3 +108,34 @@ def test_shared_scheme_edge_cases():
     torch.cuda.synchronize()
     assert torch.all(f == 7.0)
     h.free()
+
+
+def test_table1_system_full_size_sampled():
+    """Table 1's common-support system (40 x 40, 200 shared monomials, degree up to 80) at
+    8,192 points, the benchmark's launch (five row groups per 32-point tile): both schemes
+    agree at every point within the DD tolerance, and the oracle checks 6 sampled points
+    (first and last, and in different tiles)."""
+    torch = torch_cuda()
+    s, gamma = synth.common_support_system(1)
+    rng = np.random.default_rng(540)
+    npts = 8192
+    pts = synth.torus_points(rng, npts, s.n)
+    out = {}
+    for mode in (hc.HC_EVAL_SHARED, hc.HC_EVAL_PER_TERM):
+        sysh = hc.system_from(s, 2, gamma)
+        sysh.set_eval_mode(mode)
+        x = torch.from_numpy(hc.to_soa(pts, 2)).cuda()
+        f = torch.empty((2, 2, s.npoly, npts), dtype=torch.float64, device="cuda")
+        J = torch.empty((2, 2, s.npoly, s.n, npts), dtype=torch.float64, device="cuda")
+        hc.hc_eval_jac(sysh, npts, 0.5, x, f, J)
+        torch.cuda.synchronize()
+        out[mode] = (f.cpu().numpy(), J.cpu().numpy())
+        sysh.free()
+    fa, Ja = (hc.from_soa(v) for v in out[hc.HC_EVAL_SHARED])
+    fb, Jb = (hc.from_soa(v) for v in out[hc.HC_EVAL_PER_TERM])
+    assert np.all(rel_err_per_point(fa, fb) <= TOL[2]) and np.all(rel_err_per_point(Ja, Jb) <= TOL[2])
+    sample = np.array([0, 31, 32, 4099, 8000, 8191])
+    fo, Jo = oracle_eval(s, gamma, 2, limbs_of(pts[sample], 2), 0.5)
+    ef, eJ = rel_err_per_point(fa[sample], fo), rel_err_per_point(Ja[sample], Jo)
+    print(f"Table 1 system, 8,192 points: f {digits(ef):.1f} digits, J {digits(eJ):.1f} digits")
+    assert np.all(ef <= TOL[2]) and np.all(eJ <= TOL[2])
