@@ -6,14 +6,15 @@
 //
 //   begin (1 block)                      init, predictor (or end-game set-up)
 //   max_it x Newton iteration (Alg. 4.1):
-//     powers (2n blocks of 1 thread)     x_j^e, start-system terms
+//     powers (n blocks of 1 thread)      x_j^e
 //     monomials (grid)                   values and partials of every monomial -> V
+//     (beside powers .. chunks, a branch of the graph: start-system terms, n blocks of 1)
 //     entries (grid)                     sums per Jacobian entry + homotopy -> H, J
 //     lu prep (1 block of 1024)          residual, leading limbs of J
 //     ceil(n / 16) x [panel (1 block), update (grid)]   FP64 LU with partial pivoting
 //     inverse (n warps)                  the FP64 inverse, one column per warp
-//     apply (1 block)                    dz_0 = inverse x (-h)
-//     max_refine x [residual rows (n warps), apply (1 block)]   refinement in L limbs
+//     gemv (grid), apply (1 block)       dz_0 = inverse x (-h)
+//     max_refine x [residual rows (n blocks of 4 warps), gemv, apply]   refinement in L limbs
 //     update (1 block)                   z += dz, convergence test
 //   end (1 block)                        accept / step back, step size, stop tests
 //
@@ -51,6 +52,8 @@ struct GArgs {
     const double *x0;
     double *z, *zp, *zpp, *zh, *ZP, *PW, *V, *HS, *H, *JH, *B, *RV, *DZ;
     double *INV;              // [2][n][n] the inverse of the FP64 factors, column-major
+    double *D;                // [2][n] the FP64 correction of a solve or sweep
+    double *DNB;              // [ceil(n / HC_GEMV_ROWS)] its largest moduli, per block
     int32_t *PIV;
     int32_t *PSTEP;           // [n] the blocked LU's pivot row of each step
     // the entries' contribution lists cut into chunks of at most `chunk`, summed in
@@ -58,6 +61,8 @@ struct GArgs {
     const int32_t *cbeg;      // [nchunks+1] chunk c covers tlist[cbeg[c] .. cend[c])
     const int32_t *cend;
     const int32_t *eptr;      // [ne+1] the chunks of entry e: eptr[e] .. eptr[e+1]-1
+    const int32_t *eord;      // [ne] the entries with HC_GLONG chunks or more, then the rest
+    int nlong;                //      (longest first): the order of k_g_entries
     double *P;                // [2][L][nchunks] chunk sums
     int nchunks;
     hc_track_opts o;
@@ -112,23 +117,24 @@ template <int L> __global__ void __launch_bounds__(HC_TB) k_g_begin(GArgs a)
     }
 }
 
-// the start-system terms of the homotopy (blocks 0 .. n-1, one row each) and the power
-// table (blocks n .. 2n-1, one variable each): one dependent chain of complex products
-// per index, each in a block of its own so that the chains spread over the SMs (one
-// SM's FP64 pipe completes two lanes' instructions per clock; in one block of 256
-// threads they took 0.17 ms per Newton iteration at n = 96 in quad double).  The long
-// chains (x_i^(d-1) by binary powering) come first, so they start first.
+// The power table (k_g_powers, one variable per block) and the start-system terms of the
+// homotopy (k_g_terms, one row per block): one dependent chain of complex products per
+// index, each in a block of its own so that the chains spread over the SMs.  Both are
+// bound by the latency of their chains (a row's x_i^(d-1) by binary powering is about a
+// dozen quad-double products in a row: 0.14 ms at n = 96), so the terms, which only the
+// entry sums need, run in a branch of the stage graph beside the power table, the
+// monomials and the chunk sums.
 template <int L> __global__ void __launch_bounds__(1) k_g_powers(GArgs a)
+{
+    if (!g_active(*a.g)) return;
+    powers_of<L>(a.S, blockIdx.x, a.zh, a.PW);
+}
+template <int L> __global__ void __launch_bounds__(1) k_g_terms(GArgs a)
 {
     const GStage &g = *a.g;
     if (!g_active(g)) return;
-    const int n = a.S.n, q = blockIdx.x;
-    if (q < n) {
-        const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
-        homotopy_terms<L>(a.S, q, a.zh, gs, a.HS, false);
-    } else {
-        powers_of<L>(a.S, q - n, a.zh, a.PW);
-    }
+    const C<L> gs = gamma_one_minus_t<L>(a.S.gre, a.S.gim, g.t1);
+    homotopy_terms<L>(a.S, blockIdx.x, a.zh, gs, a.HS, false);
 }
 
 // one thread per monomial in one-warp blocks: all blocks are resident at once (20 or 21
@@ -143,32 +149,61 @@ template <int L> __global__ void __launch_bounds__(HC_GMONO) k_g_monomials(GArgs
     if (q < a.S.nmon) monomial_to_V<L>(a.S, __ldg(a.S.perm + q), a.zh, a.PW, a.V);
 }
 
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_chunks(GArgs a)
+// one chunk per thread, in one-warp blocks: the chunks' sums are chains of additions
+// bound by their latency, so every SM should hold the same number of warps (in
+// 128-thread blocks, 347 blocks on 152 SMs left the FP64 pipes 62 % busy over the kernel
+// against 83 % while active)
+#define HC_GCHUNK 32
+template <int L> __global__ void __launch_bounds__(HC_GCHUNK) k_g_chunks(GArgs a)
 {
     const GStage &g = *a.g;
     if (!g_active(g)) return;
-    const int c = blockIdx.x * HC_TB + threadIdx.x;
+    const int c = blockIdx.x * HC_GCHUNK + threadIdx.x;
     if (c >= a.nchunks) return;
     st_c<L>(a.P, a.nchunks, c, sum_contributions<L>(a.S, __ldg(a.cbeg + c), __ldg(a.cend + c), a.V));
 }
 
-// the chunk sums of each entry added in chunk order (an entry of one chunk takes its sum
-// as is, the same value as one sequential sum), then the homotopy
-template <int L> __global__ void __launch_bounds__(HC_TB) k_g_entries(GArgs a)
+// the chunk sums of each entry added in a fixed order, then the homotopy, in one-warp
+// blocks.  An entry of fewer than HC_GLONG chunks is one thread's, its chunks added in
+// order (an entry of one chunk takes its sum as is: the same value as one sequential sum,
+// as in the block engine).  A longer entry (the value entries of long rows: 32 chunks for
+// 1,024 terms) is one warp's: lane l adds the chunks c0 + l, c0 + l + 32, ... in order,
+// then a fixed shuffle tree adds the lanes.  In one thread each, the value entries were
+// chains of 31 quad-double additions, taken longest first by one block on one SM.
+#define HC_GLONG 8
+template <int L> __global__ void __launch_bounds__(32) k_g_entries(GArgs a)
 {
     const GStage &g = *a.g;
     if (!g_active(g)) return;
-    const int q = blockIdx.x * HC_TB + threadIdx.x;
-    const int ne = a.S.npoly * (a.S.n + 1);
+    const int lane = threadIdx.x, ne = a.S.npoly * (a.S.n + 1);
+    if ((int)blockIdx.x < a.nlong) {
+        const int e = __ldg(a.eord + blockIdx.x);
+        const int c0 = __ldg(a.eptr + e), c1 = __ldg(a.eptr + e + 1);
+        C<L> acc = c_zero<L>();
+        for (int c = c0 + lane; c < c1; c += 32) acc = c_add(acc, ld_c<L>(a.P, a.nchunks, c));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            C<L> other;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                other.re.v[l] = __shfl_down_sync(0xffffffffu, acc.re.v[l], o);
+                other.im.v[l] = __shfl_down_sync(0xffffffffu, acc.im.v[l], o);
+            }
+            acc = c_add(acc, other);
+        }
+        if (lane == 0) entry_finish<L>(a.S, e, g.t1, acc, a.HS, a.H, a.JH, nullptr);
+        return;
+    }
+    const int q = a.nlong + ((int)blockIdx.x - a.nlong) * 32 + lane;
     if (q >= ne) return;
-    const int e = __ldg(a.S.eperm + q);
+    const int e = __ldg(a.eord + q);
     const int c0 = __ldg(a.eptr + e), c1 = __ldg(a.eptr + e + 1);
     C<L> acc = ld_c<L>(a.P, a.nchunks, c0);
     for (int c = c0 + 1; c < c1; c++) acc = c_add(acc, ld_c<L>(a.P, a.nchunks, c));
     entry_finish<L>(a.S, e, g.t1, acc, a.HS, a.H, a.JH, nullptr);
 }
 
-#define HC_GLU 1024  // threads of the whole-GPU engine's LU blocks
+#define HC_GLU 1024  // threads of the LU preparation block
 
 // The residual ||h|| and ||x|| of the incoming point (leading limbs), every thread
 // getting them; returns 0 if h is not finite
@@ -191,41 +226,6 @@ template <int L> __device__ __forceinline__ int g_residual(const GArgs &a, Block
     block_max2<HC_GLU>(r2, xn, sh);
     res = sqrt(r2);
     return fin;
-}
-
-// residual of the incoming point and the FP64 LU (block_newton's first part), by one block
-// of 1024 threads: the trailing updates keep all of one SM's warps busy.  For systems too
-// large for the blocked LU's panels in shared memory.
-template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu(GArgs a, int b_smem)
-{
-    __shared__ BlockShared sh;
-    extern __shared__ double fsh[];  // (b_smem) the factors [2][n][n]
-    GStage &g = *a.g;
-    if (!g_active(g)) return;
-    const int n = a.S.n, tid = threadIdx.x;
-    double res, xn;
-    const int fin = g_residual<L>(a, sh, res, xn);
-    double cond = 0.0;
-    double *Bf = b_smem ? fsh : a.B;
-    const int status = fin ? block_lu64<L, HC_GLU>(n, a.JH, Bf, a.PIV, sh, &cond) : HC_NONFINITE;
-    if (status == HC_OK && b_smem) {
-        // the factors for the inverse
-        for (int q = tid; q < 2 * n * n; q += HC_GLU) a.B[q] = Bf[q];
-    }
-    if (tid == 0) {
-        g.res = res;
-        if (g.res_first < 0) g.res_first = res;
-        g.cond = cond;
-        g.xn = xn;
-        if (status != HC_OK) {
-            g.it++;
-            g.nst = status;
-        } else {
-            g.refine_active = 0;
-            g.prev_dn = INFINITY;
-            g.sweeps = 0;
-        }
-    }
 }
 
 // ---- The blocked FP64 LU: the same factors, pivots and condition estimate as
@@ -281,7 +281,10 @@ template <int L> __global__ void __launch_bounds__(HC_GLU, 1) k_g_lu_prep(GArgs 
     }
 }
 
-// columns kb .. kb+nb-1, rows kb .. n-1 (m rows), factored in shared memory
+// columns kb .. kb+nb-1, rows kb .. n-1 (m rows), factored in shared memory with the
+// steps of block_lu64 restricted to the panel: two barriers per column, (A) multipliers
+// and the row swap within the panel, (B) the rank-1 update of the panel's later columns,
+// which also finds the next column's pivot
 template <int L> __global__ void __launch_bounds__(HC_GPANEL) k_g_panel(GArgs a, int kb)
 {
     __shared__ BlockShared sh;
@@ -301,13 +304,15 @@ template <int L> __global__ void __launch_bounds__(HC_GPANEL) k_g_panel(GArgs a,
     auto st = [&](int i, int c, cdv v) { psh[(size_t)c * m + i] = v.re; psh[pp + (size_t)c * m + i] = v.im; };
     auto mag = [&](cdv v) { return add_(mul_(v.re, v.re), mul_(v.im, v.im)); };
     double pmax = g.pmax, pmin = g.pmin;
+    // pivot of the panel's first column: the largest squared modulus, ties to the lowest row
+    Piv pv = piv_none();
+    for (int i = tid; i < m; i += HC_GPANEL) {
+        const cdv v = ld(i, 0);
+        piv_take(pv, amax_key(mag(v)), i, v.re, v.im);
+    }
+    pv = block_argmax_piv<HC_GPANEL>(pv, sh);
     for (int c = 0; c < nb; c++) {
-        // pivot: the largest squared modulus in column c, rows c .. m-1, ties to the lowest
-        long long bk = -1;
-        int bi = 0x7fffffff;
-        for (int i = c + tid; i < m; i += HC_GPANEL) amax_take(bk, bi, amax_key(mag(ld(i, c))), i);
-        block_argmax_key<HC_GPANEL>(bk, bi, sh);
-        const double bv = amax_value(bk);
+        const double bv = amax_value(pv.k);
         if (!(bv > 0.0)) {
             if (tid == 0) {
                 g.it++;
@@ -317,9 +322,19 @@ template <int L> __global__ void __launch_bounds__(HC_GPANEL) k_g_panel(GArgs a,
         }
         pmax = fmax(pmax, bv);
         pmin = fmin(pmin, bv);
-        const int piv = bi;
+        const int piv = pv.i;
+        // (A) multipliers of column c from the rows before the swap (row piv takes the old
+        // row c's entry), the panel's other columns swapped; the pivot's reciprocal from
+        // the value carried by the search
+        cdv inv = {0.0, 0.0};
+        if (tid == 0 || c + 1 + tid < m) {
+            const double r = 1.0 / bv;
+            inv = {pv.re * r, -pv.im * r};
+        }
+        for (int i = c + 1 + tid; i < m; i += HC_GPANEL) st(i, c, cdv_mul(ld(i == piv ? c : i, c), inv));
         if (piv != c)
             for (int cc = tid; cc < nb; cc += HC_GPANEL) {
+                if (cc == c) continue;
                 const cdv t0 = ld(c, cc);
                 st(c, cc, ld(piv, cc));
                 st(piv, cc, t0);
@@ -333,24 +348,22 @@ template <int L> __global__ void __launch_bounds__(HC_GPANEL) k_g_panel(GArgs a,
             }
         }
         __syncthreads();
-        // the multipliers of column c and the pivot's reciprocal conj(a) / |a|^2 on the
-        // diagonal (formed only by the threads that use it)
-        cdv inv = {0.0, 0.0};
-        if (tid == 0 || c + 1 + tid < m) {
-            const cdv av = ld(c, c);
-            const double r = 1.0 / bv;
-            inv = {av.re * r, -av.im * r};
-        }
-        for (int i = c + 1 + tid; i < m; i += HC_GPANEL) st(i, c, cdv_mul(ld(i, c), inv));
-        __syncthreads();
+        // (B) the reciprocal on the diagonal, the rank-1 update of columns c+1 .. nb-1,
+        // the next column's pivot
         if (tid == 0) st(c, c, inv);
-        // the rank-1 update of the panel's columns c+1 .. nb-1
         const int w = m - c - 1, wc = nb - c - 1;
-        for (int idx = tid; idx < w * wc; idx += HC_GPANEL) {
-            const int cj = c + 1 + idx / w, i = c + 1 + idx % w;
-            st(i, cj, cdv_fnma(ld(i, cj), ld(i, c), ld(c, cj)));
+        pv = piv_none();
+        DivWalk dw(tid, HC_GPANEL, w > 0 ? w : 1);
+        for (int idx = tid; idx < w * wc; idx += HC_GPANEL, dw.next()) {
+            const int cj = c + 1 + dw.hi, i = c + 1 + dw.lo;
+            const cdv v = cdv_fnma(ld(i, cj), ld(i, c), ld(c, cj));
+            st(i, cj, v);
+            if (cj == c + 1) piv_take(pv, amax_key(mag(v)), i, v.re, v.im);
         }
+        warp_argmax_piv(pv);
+        piv_publish(pv, sh);
         __syncthreads();
+        pv = piv_merge<HC_GPANEL>(sh);
     }
     for (int q = tid; q < nb * m; q += HC_GPANEL) {
         const int c = q / m, r = q - c * m;
@@ -450,20 +463,20 @@ template <int L> __global__ void __launch_bounds__(HC_GINV) k_g_inverse(GArgs a,
     }
 }
 
-// d = INV r in FP64: 8 lanes per row, each summing the columns j = lane (mod 8) in order,
-// then a fixed shuffle tree.  first: r = -h (the first solve), dz = d; else r = the
-// residual of k_g_refine_rows, dz += d, and the refinement's stop test:
-// ||d|| <= 2^(-53 L) max(||x||, ||dz||) or max_refine sweeps; a d no smaller than the
-// previous one ends it without being added
-#define HC_GAPPLY 1024
-template <int L> __global__ void __launch_bounds__(HC_GAPPLY, 1) k_g_apply(GArgs a, int first)
+// d = INV r in FP64, HC_GEMV_ROWS rows per block (spread over the GPU: in one block the
+// product was bound by one SM's FP64 pipe): 8 lanes per row, each summing the columns
+// j = lane (mod 8) in order, then a fixed shuffle tree.  first: r = -h (the first solve);
+// else r = the residual of k_g_refine_rows.  d goes to D, each block's largest |d_i| to
+// DNB[block].
+#define HC_GEMV_ROWS 8
+template <int L> __global__ void __launch_bounds__(8 * HC_GEMV_ROWS) k_g_gemv(GArgs a, int first)
 {
-    __shared__ BlockShared sh;
     __shared__ double rsh[2 * 256];
-    GStage &g = *a.g;
+    __shared__ double msh[HC_GEMV_ROWS];
+    const GStage &g = *a.g;
     if (!g_active(g) || (!first && !g.refine_active)) return;
     const int n = a.S.n, tid = threadIdx.x;
-    for (int i = tid; i < n; i += HC_GAPPLY) {
+    for (int i = tid; i < n; i += 8 * HC_GEMV_ROWS) {
         if (first) {
             double re, im;
             ld_lead<L>(a.H, n, i, re, im);
@@ -476,33 +489,53 @@ template <int L> __global__ void __launch_bounds__(HC_GAPPLY, 1) k_g_apply(GArgs
     }
     __syncthreads();
     const size_t ip = (size_t)n * n;
-    __shared__ double dsh[2 * 256];  // d
-    const int q = tid & 7, rows = HC_GAPPLY / 8;
-    double dn = 0.0, zz = 0.0;
-    for (int base = 0; base < n; base += rows) {
-        const int i = base + (tid >> 3);
-        cdv d = {0.0, 0.0};
-        if (i < n)
-            for (int j = q; j < n; j += 8)
-                d = cdv_fnma(d, cdv{-a.INV[(size_t)j * n + i], -a.INV[ip + (size_t)j * n + i]}, cdv{rsh[j], rsh[n + j]});
+    const int q = tid & 7, r = tid >> 3, i = blockIdx.x * HC_GEMV_ROWS + r;
+    cdv d = {0.0, 0.0};
+    if (i < n)
+        for (int j = q; j < n; j += 8)
+            d = cdv_fnma(d, cdv{-a.INV[(size_t)j * n + i], -a.INV[ip + (size_t)j * n + i]}, cdv{rsh[j], rsh[n + j]});
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-            d.re = add_(d.re, __shfl_xor_sync(0xffffffffu, d.re, o));
-            d.im = add_(d.im, __shfl_xor_sync(0xffffffffu, d.im, o));
-        }
-        if (i < n && q == 0) {
-            dsh[i] = d.re;
-            dsh[n + i] = d.im;
-            dn = fmax(dn, sqrt(add_(mul_(d.re, d.re), mul_(d.im, d.im))));
-        }
+    for (int o = 4; o > 0; o >>= 1) {
+        d.re = add_(d.re, __shfl_xor_sync(0xffffffffu, d.re, o));
+        d.im = add_(d.im, __shfl_xor_sync(0xffffffffu, d.im, o));
     }
+    if (q == 0) {
+        double m = 0.0;
+        if (i < n) {
+            a.D[i] = d.re;
+            a.D[n + i] = d.im;
+            m = sqrt(add_(mul_(d.re, d.re), mul_(d.im, d.im)));
+        }
+        msh[r] = m;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double m = msh[0];
+        for (int k = 1; k < HC_GEMV_ROWS; k++) m = fmax(m, msh[k]);
+        a.DNB[blockIdx.x] = m;
+    }
+}
+
+// The correction of k_g_gemv applied.  first: dz = d; else dz += d, and the refinement's
+// stop test: ||d|| <= 2^(-53 L) max(||x||, ||dz||) or max_refine sweeps; a d no smaller
+// than the previous one ends it without being added
+#define HC_GAPPLY 256
+template <int L> __global__ void __launch_bounds__(HC_GAPPLY) k_g_apply(GArgs a, int first)
+{
+    __shared__ BlockShared sh;
+    GStage &g = *a.g;
+    if (!g_active(g) || (!first && !g.refine_active)) return;
+    const int n = a.S.n, tid = threadIdx.x, nb = (n + HC_GEMV_ROWS - 1) / HC_GEMV_ROWS;
+    double dn = 0.0, zz = 0.0;
+    for (int k = tid; k < nb; k += HC_GAPPLY) dn = fmax(dn, a.DNB[k]);
     dn = block_max<HC_GAPPLY>(dn, sh);
     // a refinement correction no smaller than the previous one (the residual is at its
     // rounding floor) ends the refinement without being added
     const bool apply = first || dn < g.prev_dn;
     if (apply) {
         for (int i = tid; i < n; i += HC_GAPPLY) {
-            const C<L> v = first ? c_from<L>(dsh[i], dsh[n + i]) : c_add(ld_c<L>(a.DZ, n, i), c_from<L>(dsh[i], dsh[n + i]));
+            const C<L> d = c_from<L>(a.D[i], a.D[n + i]);
+            const C<L> v = first ? d : c_add(ld_c<L>(a.DZ, n, i), d);
             st_c<L>(a.DZ, n, i, v);
             zz = fmax(zz, sqrt(c_abs2_lead(v)));
         }
@@ -520,15 +553,20 @@ template <int L> __global__ void __launch_bounds__(HC_GAPPLY, 1) k_g_apply(GArgs
     }
 }
 
-// r_i = -h_i - sum_j J_ij dz_j in L limbs, one block of 32 per row; each lane sums a
-// strided part of the row, then a fixed shuffle tree adds the 32 parts
-template <int L> __global__ void __launch_bounds__(32) k_g_refine_rows(GArgs a)
+// r_i = -h_i - sum_j J_ij dz_j in L limbs, one block of HC_GREF threads per row: each
+// thread takes the columns j = tid (mod HC_GREF), a fixed shuffle tree adds a warp's
+// parts, and thread 0 adds the warps' sums in warp order.  The row's quad-double chain is
+// what bounds this kernel (one warp per row: three products and five additions in a row,
+// 75 us a sweep at n = 96); spreading the columns over four warps shortens it.
+#define HC_GREF 128
+template <int L> __global__ void __launch_bounds__(HC_GREF) k_g_refine_rows(GArgs a)
 {
+    __shared__ double part[HC_GREF / 32][2 * L];
     const GStage &g = *a.g;
     if (!g_active(g) || !g.refine_active) return;
-    const int n = a.S.n, i = blockIdx.x, lane = threadIdx.x;
+    const int n = a.S.n, i = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     C<L> acc = c_zero<L>();
-    for (int j = lane; j < n; j += 32)
+    for (int j = threadIdx.x; j < n; j += HC_GREF)
         acc = c_fnma(acc, ld_c<L>(a.JH, (size_t)n * n, (size_t)i * n + j), ld_c<L>(a.DZ, n, j));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -540,7 +578,23 @@ template <int L> __global__ void __launch_bounds__(32) k_g_refine_rows(GArgs a)
         }
         acc = c_add(acc, other);
     }
-    if (lane == 0) {
+    if (lane == 0)
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            part[w][l] = acc.re.v[l];
+            part[w][L + l] = acc.im.v[l];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < HC_GREF / 32; q++) {
+            C<L> other;
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                other.re.v[l] = part[q][l];
+                other.im.v[l] = part[q][L + l];
+            }
+            acc = c_add(acc, other);
+        }
         // acc = -sum_j J_ij dz_j, so r = acc - h_i
         const C<L> r = c_sub(acc, ld_c<L>(a.H, n, i));
         a.RV[i] = r.re.v[0];
@@ -614,50 +668,71 @@ template <int L>
 static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t cs, cudaGraphExec_t *exec)
 {
     const int mblocks = (a.S.nmon + HC_GMONO - 1) / HC_GMONO;
-    const int eblocks = (a.S.npoly * (a.S.n + 1) + HC_TB - 1) / HC_TB;
-    // the FP64 LU, and each column solve of the inverse, from shared memory when the
-    // factors fit (n <= 110)
+    const int eblocks = a.nlong + (a.S.npoly * (a.S.n + 1) - a.nlong + 31) / 32;
+    // each column solve of the inverse from a shared-memory copy of the factors when they
+    // fit (n <= 110)
     const size_t bsm = sizeof(double) * 2 * (size_t)a.S.n * a.S.n;
     const size_t vec4 = sizeof(double) * 4 * (size_t)a.S.n;
     const int b_smem = vec4 + bsm <= 200 * 1024;
-    const size_t lu_bytes = b_smem ? bsm : 0, inv_bytes = vec4 + (b_smem ? bsm : 0);
-    // the blocked LU while a panel and the update kernel's copies fit in shared memory
+    const size_t inv_bytes = vec4 + (b_smem ? bsm : 0);
+    // the blocked LU's panel and the update kernel's copies in shared memory (at most
+    // 82 KB for the tracker's n <= 256)
     const int n = a.S.n, nb0 = n < HC_GLU_NB ? n : HC_GLU_NB;
     auto panel_bytes = [&](int m, int nb) { return sizeof(double) * 2 * (size_t)nb * m; };
     auto upd_bytes = [&](int m, int nb) { return sizeof(double) * 2 * (size_t)m * (nb + HC_GUPD); };
-    const bool blocked = upd_bytes(n, nb0) <= 200 * 1024;
-    cudaError_t ea = cudaFuncSetAttribute(k_g_lu<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(lu_bytes > 0 ? lu_bytes : 1));
+    cudaError_t ea = cudaFuncSetAttribute(k_g_inverse<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_bytes);
     if (ea == cudaSuccess)
-        ea = cudaFuncSetAttribute(k_g_inverse<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_bytes);
-    if (ea == cudaSuccess && blocked)
         ea = cudaFuncSetAttribute(k_g_panel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_bytes(n, nb0));
-    if (ea == cudaSuccess && blocked)
+    if (ea == cudaSuccess)
         ea = cudaFuncSetAttribute(k_g_lu_update<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_bytes(n, nb0));
     if (ea != cudaSuccess) return hc_cuda_fail(ea, "whole-GPU engine shared memory");
+    // the branch of the start-system terms: a second stream forked from and joined back
+    // into the capturing stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    auto release = [&]() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
+    };
+    if (e != cudaSuccess) {
+        release();
+        return hc_cuda_fail(e, "whole-GPU engine: graph branch stream");
+    }
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return hc_cuda_fail(e, "cudaStreamBeginCapture");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        release();
+        return hc_cuda_fail(e, "cudaStreamBeginCapture");
+    }
     k_g_begin<L><<<1, HC_TB, 0, cs>>>(a);
     for (int it = 0; it < max_it; it++) {
-        k_g_powers<L><<<2 * a.S.n, 1, 0, cs>>>(a);
+        cudaEventRecord(fork, cs);
+        cudaStreamWaitEvent(side, fork, 0);
+        k_g_terms<L><<<a.S.n, 1, 0, side>>>(a);
+        cudaEventRecord(join, side);
+        k_g_powers<L><<<a.S.n, 1, 0, cs>>>(a);
         k_g_monomials<L><<<mblocks > 0 ? mblocks : 1, HC_GMONO, 0, cs>>>(a);
-        k_g_chunks<L><<<(a.nchunks + HC_TB - 1) / HC_TB, HC_TB, 0, cs>>>(a);
-        k_g_entries<L><<<eblocks, HC_TB, 0, cs>>>(a);
-        if (blocked) {
-            k_g_lu_prep<L><<<1, HC_GLU, 0, cs>>>(a);
-            for (int kb = 0; kb < n; kb += HC_GLU_NB) {
-                const int m = n - kb, nb = m < HC_GLU_NB ? m : HC_GLU_NB, others = n - nb;
-                k_g_panel<L><<<1, HC_GPANEL, panel_bytes(m, nb), cs>>>(a, kb);
-                if (others > 0)
-                    k_g_lu_update<L><<<(others + HC_GUPD - 1) / HC_GUPD, 32 * HC_GUPD, upd_bytes(m, nb), cs>>>(a, kb);
-            }
-        } else {
-            k_g_lu<L><<<1, HC_GLU, lu_bytes, cs>>>(a, b_smem);
+        k_g_chunks<L><<<(a.nchunks + HC_GCHUNK - 1) / HC_GCHUNK, HC_GCHUNK, 0, cs>>>(a);
+        cudaStreamWaitEvent(cs, join, 0);
+        k_g_entries<L><<<eblocks, 32, 0, cs>>>(a);
+        k_g_lu_prep<L><<<1, HC_GLU, 0, cs>>>(a);
+        for (int kb = 0; kb < n; kb += HC_GLU_NB) {
+            const int m = n - kb, nb = m < HC_GLU_NB ? m : HC_GLU_NB, others = n - nb;
+            k_g_panel<L><<<1, HC_GPANEL, panel_bytes(m, nb), cs>>>(a, kb);
+            if (others > 0)
+                k_g_lu_update<L><<<(others + HC_GUPD - 1) / HC_GUPD, 32 * HC_GUPD, upd_bytes(m, nb), cs>>>(a, kb);
         }
         k_g_inverse<L><<<a.S.n, HC_GINV, inv_bytes, cs>>>(a, b_smem);
+        const int gblocks = (a.S.n + HC_GEMV_ROWS - 1) / HC_GEMV_ROWS;
+        k_g_gemv<L><<<gblocks, 8 * HC_GEMV_ROWS, 0, cs>>>(a, 1);
         k_g_apply<L><<<1, HC_GAPPLY, 0, cs>>>(a, 1);
         for (int r = 0; r < max_refine; r++) {
-            k_g_refine_rows<L><<<a.S.n, 32, 0, cs>>>(a);
+            k_g_refine_rows<L><<<a.S.n, HC_GREF, 0, cs>>>(a);
+            k_g_gemv<L><<<gblocks, 8 * HC_GEMV_ROWS, 0, cs>>>(a, 0);
             k_g_apply<L><<<1, HC_GAPPLY, 0, cs>>>(a, 0);
         }
         k_g_update<L><<<1, HC_TB, 0, cs>>>(a);
@@ -666,6 +741,7 @@ static int grid_capture(const GArgs &a, int max_it, int max_refine, cudaStream_t
     e = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
+    release();
     if (e != cudaSuccess) return hc_cuda_fail(e, "capturing the stage graph");
     return HC_SUCCESS;
 }
@@ -694,7 +770,8 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     const size_t o_pw = put(vec * (s->max_exp > 2 ? s->max_exp - 2 : 1));
     const size_t o_v = put(sizeof(double) * 2 * L * (vplane > 0 ? vplane : 1));
     const size_t o_hs = put(3 * vec), o_h = put(vec), o_jh = put(vec * n), o_b = put(sizeof(double) * 2 * (size_t)n * n),
-                 o_inv = put(sizeof(double) * 2 * (size_t)n * n);
+                 o_inv = put(sizeof(double) * 2 * (size_t)n * n), o_d = put(sizeof(double) * 2 * (size_t)n),
+                 o_dnb = put(sizeof(double) * ((size_t)n + HC_GEMV_ROWS - 1) / HC_GEMV_ROWS);
     const size_t o_rv = put(sizeof(double) * 2 * (size_t)n), o_dz = put(vec), o_piv = put(sizeof(int32_t) * n),
                  o_pstep = put(sizeof(int32_t) * n);
     // chunks of the entries' contribution lists (from the transpose table's offsets)
@@ -712,8 +789,18 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
         eptr[e + 1] = (int32_t)cbeg.size();
     }
     const int nchunks = (int)cbeg.size();
+    // the order of k_g_entries: the long entries (one warp each), then the others in the
+    // system's longest-first order (one thread each)
+    std::vector<int32_t> eperm((size_t)ne), eord;
+    HC_CUDA_TRY(cudaMemcpy(eperm.data(), s->dev.eperm, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost));
+    for (int e = 0; e < ne; e++)
+        if (eptr[e + 1] - eptr[e] >= HC_GLONG) eord.push_back(e);
+    const int nlong = (int)eord.size();
+    for (int q = 0; q < ne; q++)
+        if (eptr[eperm[q] + 1] - eptr[eperm[q]] < HC_GLONG) eord.push_back(eperm[q]);
     const size_t o_cb = put(sizeof(int32_t) * nchunks), o_ce = put(sizeof(int32_t) * nchunks),
-                 o_ep = put(sizeof(int32_t) * (ne + 1)), o_p = put(sizeof(double) * 2 * L * (size_t)nchunks);
+                 o_ep = put(sizeof(int32_t) * (ne + 1)), o_eo = put(sizeof(int32_t) * ne),
+                 o_p = put(sizeof(double) * 2 * L * (size_t)nchunks);
     void *ws = nullptr;
     HC_CUDA_TRY(cudaMalloc(&ws, off));
     char *b = (char *)ws;
@@ -734,6 +821,8 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     a.JH = (double *)(b + o_jh);
     a.B = (double *)(b + o_b);
     a.INV = (double *)(b + o_inv);
+    a.D = (double *)(b + o_d);
+    a.DNB = (double *)(b + o_dnb);
     a.RV = (double *)(b + o_rv);
     a.DZ = (double *)(b + o_dz);
     a.PIV = (int32_t *)(b + o_piv);
@@ -741,6 +830,8 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     a.cbeg = (const int32_t *)(b + o_cb);
     a.cend = (const int32_t *)(b + o_ce);
     a.eptr = (const int32_t *)(b + o_ep);
+    a.eord = (const int32_t *)(b + o_eo);
+    a.nlong = nlong;
     a.P = (double *)(b + o_p);
     a.nchunks = nchunks;
     a.o = *o;
@@ -759,6 +850,7 @@ int hc_track_grid_path(const hc_system *s, const double *x0, double *x1, double 
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_cb, cbeg.data(), sizeof(int32_t) * nchunks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_ce, cend.data(), sizeof(int32_t) * nchunks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_ep, eptr.data(), sizeof(int32_t) * (ne + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_eo, eord.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(ready, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
     if (e != cudaSuccess) rc = hc_cuda_fail(e, "grid tracker set-up");

@@ -33,6 +33,8 @@ struct BlockShared {
     double rv2[HC_TWMAX];
     long long rk[HC_TWMAX];
     int ri[HC_TWMAX];
+    double pre[HC_TWMAX];  // the pivot candidates' values (block_argmax_piv)
+    double pim[HC_TWMAX];
     double bc[4];
     int ibc[4];
 };
@@ -111,6 +113,70 @@ template <int TB> __device__ __forceinline__ void merge_argmax_key(const long lo
     }
     k = __shfl_sync(0xffffffffu, k, 0);
     i = __shfl_sync(0xffffffffu, i, 0);
+}
+
+// A pivot candidate: integer key, row, and the FP64 value itself, which travels with the
+// winner, so that the elimination step takes the pivot from registers instead of reading
+// the matrix entry that the same step overwrites with a multiplier
+struct Piv {
+    long long k;
+    int i;
+    double re, im;
+};
+__device__ __forceinline__ Piv piv_none() { return Piv{-1LL, 0x7fffffff, 0.0, 0.0}; }
+__device__ __forceinline__ void piv_take(Piv &p, long long k2, int i2, double re2, double im2)
+{
+    if (k2 > p.k || (k2 == p.k && i2 < p.i)) p = Piv{k2, i2, re2, im2};
+}
+__device__ __forceinline__ void warp_argmax_piv(Piv &p)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long k2 = __shfl_xor_sync(0xffffffffu, p.k, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, p.i, o);
+        const double re2 = __shfl_xor_sync(0xffffffffu, p.re, o);
+        const double im2 = __shfl_xor_sync(0xffffffffu, p.im, o);
+        piv_take(p, k2, i2, re2, im2);
+    }
+}
+// the warps' candidates published by warp_argmax_piv + piv_publish, merged after a barrier
+__device__ __forceinline__ void piv_publish(const Piv &p, BlockShared &sh)
+{
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        sh.rk[w] = p.k;
+        sh.ri[w] = p.i;
+        sh.pre[w] = p.re;
+        sh.pim[w] = p.im;
+    }
+}
+template <int TB> __device__ __forceinline__ Piv piv_merge(const BlockShared &sh)
+{
+    constexpr int NW = TB / 32;
+    if (NW == 1) return Piv{sh.rk[0], sh.ri[0], sh.pre[0], sh.pim[0]};
+    const int lane = threadIdx.x & 31;
+    Piv p = lane < NW ? Piv{sh.rk[lane], sh.ri[lane], sh.pre[lane], sh.pim[lane]} : piv_none();
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) {
+        const long long k2 = __shfl_xor_sync(0xffffffffu, p.k, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, p.i, o);
+        const double re2 = __shfl_xor_sync(0xffffffffu, p.re, o);
+        const double im2 = __shfl_xor_sync(0xffffffffu, p.im, o);
+        piv_take(p, k2, i2, re2, im2);
+    }
+    p.k = __shfl_sync(0xffffffffu, p.k, 0);
+    p.i = __shfl_sync(0xffffffffu, p.i, 0);
+    p.re = __shfl_sync(0xffffffffu, p.re, 0);
+    p.im = __shfl_sync(0xffffffffu, p.im, 0);
+    return p;
+}
+template <int TB> __device__ __forceinline__ Piv block_argmax_piv(Piv p, BlockShared &sh)
+{
+    warp_argmax_piv(p);
+    __syncthreads();
+    piv_publish(p, sh);
+    __syncthreads();
+    return piv_merge<TB>(sh);
 }
 
 // max over the block of TB threads; every thread gets the same value
@@ -433,35 +499,31 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
     auto st = [&](int i, int j, cdv v) { B[(size_t)j * n + i] = v.re; B[ap + (size_t)j * n + i] = v.im; };
     auto mag = [&](cdv a) { return add_(mul_(a.re, a.re), mul_(a.im, a.im)); };
     // pivot of column 0
-    long long bk = -1;
-    int bi = 0x7fffffff;
+    Piv pv = piv_none();
     for (int i = tid; i < n; i += TB) {
-        const long long key = amax_key(mag(ld(i, 0)));
-        if (key > bk) {
-            bk = key;
-            bi = i;
-        }
+        const cdv v = ld(i, 0);
+        piv_take(pv, amax_key(mag(v)), i, v.re, v.im);
     }
-    block_argmax_key<TB>(bk, bi, sh);
+    pv = block_argmax_piv<TB>(pv, sh);
     double pmax = 0.0, pmin = INFINITY;
     // Two barriers per column: (A) multipliers and row swap, (B) trailing update, which also
     // finds the next column's pivot (its warps' candidates meet after the barrier)
     for (int k = 0; k < n; k++) {
-        const double bv = amax_value(bk);
+        const double bv = amax_value(pv.k);
         if (!(bv > 0.0)) return HC_SINGULAR;
         pmax = fmax(pmax, bv);
         pmin = fmin(pmin, bv);
-        const int piv = bi;
+        const int piv = pv.i;
         // (A) the pivot row's value moves to row k: multipliers of column k from the rows
-        // before the swap (row piv takes the old row k's entry), the other columns swapped
-        // the pivot's reciprocal conj(a) / |a|^2, formed only by the threads that use it (a
-        // division is a long FP64 sequence: every thread of a large block forming it would
-        // cost more than the factorisation itself)
+        // before the swap (row piv takes the old row k's entry), the other columns swapped.
+        // The pivot's reciprocal conj(a) / |a|^2 is formed only by the threads that use it
+        // (a division is a long FP64 sequence: every thread of a large block forming it
+        // would cost more than the factorisation itself), from the pivot value carried by
+        // the search (entry (piv, k) is overwritten by a multiplier in this phase)
         cdv inv = {0.0, 0.0};
         if (tid == 0 || k + 1 + tid < n) {
-            const cdv a = ld(piv, k);
             const double r = 1.0 / bv;
-            inv = {a.re * r, -a.im * r};
+            inv = {pv.re * r, -pv.im * r};
         }
         for (int i = k + 1 + tid; i < n; i += TB) st(i, k, cdv_mul(ld(i == piv ? k : i, k), inv));
         if (piv != k) {
@@ -481,22 +543,18 @@ __device__ int block_lu64(int n, const double *__restrict__ A, double *__restric
         // (B) the reciprocal on the diagonal, the trailing update, the next pivot
         if (tid == 0) st(k, k, inv);
         const int w = n - k - 1;
-        bk = -1;
-        bi = 0x7fffffff;
+        pv = piv_none();
         DivWalk dw(tid, TB, w > 0 ? w : 1);
         for (int idx = tid; idx < w * w; idx += TB, dw.next()) {
             const int j = k + 1 + dw.hi, i = k + 1 + dw.lo;
             const cdv v = cdv_fnma(ld(i, j), ld(i, k), ld(k, j));
             st(i, j, v);
-            if (j == k + 1) amax_take(bk, bi, amax_key(mag(v)), i);
+            if (j == k + 1) piv_take(pv, amax_key(mag(v)), i, v.re, v.im);
         }
-        warp_argmax_key(bk, bi);
-        if ((tid & 31) == 0) {
-            sh.rk[tid >> 5] = bk;
-            sh.ri[tid >> 5] = bi;
-        }
+        warp_argmax_piv(pv);
+        piv_publish(pv, sh);
         __syncthreads();
-        merge_argmax_key<TB>(sh.rk, sh.ri, bk, bi);
+        pv = piv_merge<TB>(sh);
     }
     *cond = 0.5 * log10(pmax / pmin);
     return HC_OK;
