@@ -251,8 +251,9 @@ def tracker_bench(torch, hc, synth, peak_gops=None, npaths=608, uneven_paths=243
     # its paths capped at 40 stages (its rate per stage does not depend on the cap); the
     # regular variant, one wave of paths run to their ends whose makespan is set by the
     # longest, on the whole run with three shapes
-    tune = {"uneven": (dict(max_steps=40), [(t, b, 0) for t in (64, 128, 256) for b in (0, 2, 3)]),
-            "uneven_regular": (dict(predictor=hc.HC_PRED_QUADRATIC), [(128, 0, 0), (256, 0, 0), (256, 1, 0)])}
+    tune = {"uneven": (dict(max_steps=40), [(t, b, 0) for t in (64, 128, 256) for b in (0, 2, 3)] + [(512, 0, 0)]),
+            "uneven_regular": (dict(predictor=hc.HC_PRED_QUADRATIC),
+                               [(128, 0, 0), (256, 0, 0), (256, 1, 0), (512, 0, 0)])}
     out = {}
     for name, (fam, extra) in fams.items():
         systems, gammas = [f[0] for f in fam], [f[1] for f in fam]

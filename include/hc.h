@@ -140,9 +140,9 @@ int hc_set_tiles(int rows_per_task, int blocks_per_sm);
 /*
  * hc_set_track_tiles -- execution shape of hc_track_path / hc_track_resume for every
  * later call in this process (the tracker autotuner's knobs; 0 = automatic):
- *   threads_per_block  threads of a path's block: 64, 128 (automatic) or 256; the
- *                      register budget per thread stays that of 512 (double, DD) or 384
- *                      (QD) threads per SM
+ *   threads_per_block  threads of a path's block: 64, 128 (automatic), 256 or 512 (double
+ *                      and DD; QD runs 512 as 256); the register budget per thread stays
+ *                      that of 512 (double, DD) or 384 (QD) threads per SM
  *   blocks_per_sm      path blocks resident per SM, at most what occupancy allows
  *   factors            0 or 1: the FP64 factors of a path in shared memory when a block's
  *                      share of the SM holds them (else global memory); 2: always global

@@ -89,7 +89,7 @@ def tune_eval(sysh: "hc.System", x, f, J, npts: int, t: float = 0.5, reps: int =
 
 # tracker shapes searched: threads per path block x blocks per SM (0: all that fit) x
 # FP64 factors in shared (0) or global (2) memory
-TRACK_TB = (64, 128, 256)
+TRACK_TB = (64, 128, 256, 512)
 TRACK_BPS = (0, 2, 3, 4, 6)
 TRACK_FACTORS = (0, 2)
 GRID_CHUNKS = (16, 32, 64, 128)

@@ -86,21 +86,27 @@ static int check_opts(const hc_track_opts *o)
 }
 
 // Tiles of the tracker (hc_set_track_tiles), process-wide; 0 = automatic.
-static int g_track_tb = 0;       // threads per path block: 64, 128 or 256
+static int g_track_tb = 0;       // threads per path block: 64, 128, 256 or 512
 static int g_track_bps = 0;      // path blocks per SM (capped by occupancy)
 static int g_track_factors = 0;  // 0/1: FP64 factors in shared memory when they fit; 2: global
 static int g_grid_chunk = 0;     // contributions per chunk of the whole-GPU engine's entry sums
 
+// 512-thread blocks exist for double and double-double only (a quad-double block of 512
+// threads would have to live in 128 registers a thread and spill); quad double runs 256
 template <int L> static int launch_track(int tb, TrackArgs &a, int grid, int persistent, size_t smem, cudaStream_t st)
 {
+    if constexpr (L <= 2)
+        if (tb == 512) return track_launch<L, 512>(a, grid, persistent, smem, st);
     return tb == 64 ? track_launch<L, 64>(a, grid, persistent, smem, st)
-         : tb == 256 ? track_launch<L, 256>(a, grid, persistent, smem, st)
+         : tb >= 256 ? track_launch<L, 256>(a, grid, persistent, smem, st)
                      : track_launch<L, 128>(a, grid, persistent, smem, st);
 }
 
 template <int L> static int occupancy_track(int tb, size_t smem)
 {
-    return tb == 64 ? track_occupancy<L, 64>(smem) : tb == 256 ? track_occupancy<L, 256>(smem)
+    if constexpr (L <= 2)
+        if (tb == 512) return track_occupancy<L, 512>(smem);
+    return tb == 64 ? track_occupancy<L, 64>(smem) : tb >= 256 ? track_occupancy<L, 256>(smem)
                                                    : track_occupancy<L, 128>(smem);
 }
 
@@ -113,8 +119,9 @@ static int launch_track_any(int L, int tb, TrackArgs &a, int grid, int persisten
 
 extern "C" int hc_set_track_tiles(int threads_per_block, int blocks_per_sm, int factors, int grid_chunk)
 {
-    if (threads_per_block != 0 && threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256)
-        return hc_fail(HC_EINVAL, "threads_per_block must be 0, 64, 128 or 256");
+    if (threads_per_block != 0 && threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256 &&
+        threads_per_block != 512)
+        return hc_fail(HC_EINVAL, "threads_per_block must be 0, 64, 128, 256 or 512");
     if (blocks_per_sm < 0 || blocks_per_sm > 32) return hc_fail(HC_EINVAL, "blocks_per_sm out of [0, 32]");
     if (factors < 0 || factors > 2) return hc_fail(HC_EINVAL, "factors must be 0, 1 or 2");
     if (grid_chunk < 0 || grid_chunk > 4096) return hc_fail(HC_EINVAL, "grid_chunk out of [0, 4096]");

@@ -200,6 +200,21 @@ template <int L, int TB> int track_occupancy(size_t smem);
     template <> int track_occupancy<2, TB>(size_t smem) { return track_occ_of(k_track<2, TB>, TB, smem); } \
     template <> int track_occupancy<4, TB>(size_t smem) { return track_occ_of(k_track<4, TB>, TB, smem); }
 
+// double and double-double only (512-thread blocks)
+#define HC_TRACK_INSTANTIATE_D_DD(TB)                                                                    \
+    template <> int track_launch<1, TB>(TrackArgs & a, int grid, int persistent, size_t smem, cudaStream_t st) \
+    {                                                                                                     \
+        k_track<1, TB><<<grid, TB, smem, st>>>(a, persistent);                                          \
+        return HC_SUCCESS;                                                                                \
+    }                                                                                                     \
+    template <> int track_launch<2, TB>(TrackArgs & a, int grid, int persistent, size_t smem, cudaStream_t st) \
+    {                                                                                                     \
+        k_track<2, TB><<<grid, TB, smem, st>>>(a, persistent);                                          \
+        return HC_SUCCESS;                                                                                \
+    }                                                                                                     \
+    template <> int track_occupancy<1, TB>(size_t smem) { return track_occ_of(k_track<1, TB>, TB, smem); } \
+    template <> int track_occupancy<2, TB>(size_t smem) { return track_occ_of(k_track<2, TB>, TB, smem); }
+
 // blocks per SM of kernel k at this dynamic shared memory size (which is opted into first)
 template <typename K> inline int track_occ_of(K k, int tb, size_t smem)
 {

@@ -202,12 +202,15 @@ def test_struct_layouts_match_the_header(tmp_path):
 
 
 def test_track_tiles_reject_bad_shapes():
-    """hc_set_track_tiles accepts 0 (automatic) or 64 / 128 / 256 threads per block, 0..32
+    """hc_set_track_tiles accepts 0 (automatic) or 64 / 128 / 256 / 512 threads per block, 0..32
     blocks per SM, factor placement 0..2 and a chunk of 0..4096; anything else is HC_EINVAL
     and leaves the setting as it was.  Host-side only."""
     lib = hc.load()
     assert lib.hc_set_track_tiles(128, 4, 2, 64) == hc.HC_SUCCESS
-    for bad in ((96, 0, 0, 0), (-1, 0, 0, 0), (0, 33, 0, 0), (0, 0, 3, 0), (0, 0, 0, -1), (0, 0, 0, 5000)):
+    assert lib.hc_set_track_tiles(512, 1, 0, 0) == hc.HC_SUCCESS
+    assert lib.hc_set_track_tiles(128, 4, 2, 64) == hc.HC_SUCCESS
+    for bad in ((96, 0, 0, 0), (-1, 0, 0, 0), (1024, 0, 0, 0), (0, 33, 0, 0), (0, 0, 3, 0), (0, 0, 0, -1),
+                (0, 0, 0, 5000)):
         assert lib.hc_set_track_tiles(*bad) == hc.HC_EINVAL, bad
     assert hc.hc_get_track_tiles() == {"threads_per_block": 128, "blocks_per_sm": 4, "factors": 2, "grid_chunk": 64}
     hc.hc_set_track_tiles(0, 0, 0, 0)

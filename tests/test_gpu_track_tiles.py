@@ -1,5 +1,6 @@
 """The tracker's execution shape (hc_set_track_tiles; the tracker autotuner's knobs):
-threads per path block (64 / 128 / 256), path blocks per SM and the FP64 factors in
+threads per path block (64 / 128 / 256 / 512; quad double runs 512 as 256), path blocks
+per SM and the FP64 factors in
 shared or global memory change nothing in the results, bit for bit -- statuses,
 statistics, end points and step logs -- in the persistent and the graph-stepped modes;
 the whole-GPU engine's chunk length changes only the order of an entry's additions
@@ -34,7 +35,7 @@ def test_block_engine_shapes_give_identical_results(L, mode):
     try:
         hc.hc_set_track_tiles(0, 0, 0, 0)
         ref = gpu_track(torch, systems, gammas, L, opts, log_cap=160)
-        for tb in (64, 128, 256):
+        for tb in (64, 128, 256, 512):
             for bps in (0, 2):
                 for factors in (0, 2):
                     hc.hc_set_track_tiles(tb, bps, factors, 0)
