@@ -137,13 +137,13 @@ int hc_check_eval_args(const hc_system *s, int npts, double t)
 }
 
 int hc_eval_dispatch(hc_system *s, int npts, double t, const double *x, double *pw, double *f,
-                     double *J, const EvalTiles &tiles, cudaStream_t st)
+                     double *J, double *part, const EvalTiles &tiles, cudaStream_t st)
 {
     if (s->eval_shared) {
         switch (s->prec) {
-        case 1: return launch_eval_shared<1>(s->dev, npts, t, x, pw, f, J, st);
-        case 2: return launch_eval_shared<2>(s->dev, npts, t, x, pw, f, J, st);
-        case 4: return launch_eval_shared<4>(s->dev, npts, t, x, pw, f, J, st);
+        case 1: return launch_eval_shared<1>(s, npts, t, x, pw, f, J, part, st);
+        case 2: return launch_eval_shared<2>(s, npts, t, x, pw, f, J, part, st);
+        case 4: return launch_eval_shared<4>(s, npts, t, x, pw, f, J, part, st);
         }
     }
     switch (s->prec) {
@@ -165,9 +165,11 @@ extern "C" int hc_eval_jac(hc_system *s, int npts, double t, const double *x, do
     if (npts == 0) return HC_SUCCESS;
     if (!x || !f) return hc_fail(HC_EINVAL, "x or f is NULL");
     void *ws = NULL;
-    rc = hc_workspace(s, hc_pw_bytes(s, npts), &ws);
+    const size_t pwb = hc_pw_bytes(s, npts), partb = hc_shared_part_bytes(s, npts, J != NULL);
+    rc = hc_workspace(s, pwb + partb, &ws);
     if (rc) return rc;
-    return hc_eval_dispatch(s, npts, t, x, (double *)ws, f, J, g_eval_tiles, (cudaStream_t)stream);
+    double *part = partb ? (double *)((char *)ws + pwb) : NULL;
+    return hc_eval_dispatch(s, npts, t, x, (double *)ws, f, J, part, g_eval_tiles, (cudaStream_t)stream);
 }
 
 extern "C" int hc_set_tiles(int rows_per_task, int blocks_per_sm)

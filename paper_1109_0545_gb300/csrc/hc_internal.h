@@ -38,6 +38,8 @@ struct DevSys {
     const int32_t *term_row;  // [nmon] the polynomial of term m
     const int32_t *cptr;      // [npoly+1] into cterm
     const int32_t *cterm;     // constant terms (k = 0) of each polynomial, increasing
+    const double *ucost;      // [nuniq+1] prefix sums of the distinct monomials' FP64 cost
+                              // (evaluation and uses), to cut them into balanced groups
 };
 
 struct hc_system {

@@ -5,6 +5,8 @@
 // whose solution is refined with residuals in the working precision.
 #include "hc_eval.cuh"
 
+size_t hc_newton_core_bytes(const hc_system *s, int npts, int lu_mode);  // below
+
 namespace hc {
 
 // max_i |h_i| from the leading limbs (re^2 + im^2 in double, as the pivot measure);
@@ -294,7 +296,9 @@ int launch_newton(hc_system *s, int npts, double t, double *X, int lu_mode, int 
     double *PW = (double *)ws;
     double *H = (double *)(ws + pw);
     double *A = (double *)(ws + pw + hb);
-    int rc = s->eval_shared ? launch_eval_shared<L>(s->dev, npts, t, X, PW, H, A, st)
+    // the shared scheme's partial sums after everything else
+    double *part = hc_shared_part_bytes(s, npts, true) ? (double *)(ws + hc_newton_core_bytes(s, npts, lu_mode)) : nullptr;
+    int rc = s->eval_shared ? launch_eval_shared<L>(s, npts, t, X, PW, H, A, part, st)
                             : launch_eval<L>(s->dev, npts, t, X, PW, H, A, tiles, st);
     if (rc) return rc;
     const int block = 64, grid = (npts + block - 1) / block;
@@ -321,7 +325,7 @@ int launch_newton(hc_system *s, int npts, double t, double *X, int lu_mode, int 
 
 using namespace hc;
 
-size_t hc_newton_ws_bytes(const hc_system *s, int npts, int lu_mode)
+size_t hc_newton_core_bytes(const hc_system *s, int npts, int lu_mode)
 {
     const size_t n = s->n, L = s->prec;
     size_t b = hc_pw_bytes(s, npts);
@@ -334,6 +338,11 @@ size_t hc_newton_ws_bytes(const hc_system *s, int npts, int lu_mode)
         b += hc_align256(sizeof(int32_t) * n * npts);             // pivots
     }
     return b;
+}
+
+size_t hc_newton_ws_bytes(const hc_system *s, int npts, int lu_mode)
+{
+    return hc_newton_core_bytes(s, npts, lu_mode) + hc_shared_part_bytes(s, npts, true);
 }
 
 int hc_check_newton_args(const hc_system *s, int npts, double t, const double *x, int lu_mode,

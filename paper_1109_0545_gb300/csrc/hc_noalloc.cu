@@ -62,5 +62,6 @@ extern "C" int hc_eval_jac_noalloc(hc_system *s, int npts, double t, const doubl
     if (rc) return rc;
     // The power table is written in full by this call before it is read, so the previous
     // call's contents need no clearing.
-    return hc_eval_dispatch(s, npts, t, x, pw, f, J, hc_eval_tiles(), (cudaStream_t)stream);
+    // (the shared scheme runs its row groups here: no room for partial sums)
+    return hc_eval_dispatch(s, npts, t, x, pw, f, J, NULL, hc_eval_tiles(), (cudaStream_t)stream);
 }

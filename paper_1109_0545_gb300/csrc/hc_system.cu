@@ -372,6 +372,12 @@ static int build_shared_tables(hc_system *s)
     ops_shared += 6.0 * npoly * (s->n + 1);
     const int nuniq = (int)first.size();
     std::vector<int32_t> uvar_ptr((size_t)nuniq + 1, 0), uvar_pack, uuse_ptr((size_t)nuniq + 1, 0), uuse;
+    // FP64 cost of each distinct monomial (evaluation, then 36 a partial or value per use)
+    std::vector<double> ucost((size_t)nuniq + 1, 0.0);
+    for (int m = 0; m < nmon; m++)
+        if (uid[m] >= 0) ucost[uid[m] + 1] += 36.0 * (vp[m + 1] - vp[m] + 1);
+    for (int u = 0; u < nuniq; u++)
+        ucost[u + 1] += ucost[u] + monomial_ops(pack + vp[first[u]], vp[first[u] + 1] - vp[first[u]], false);
     for (int u = 0; u < nuniq; u++) {
         const int m = first[u];
         uvar_pack.insert(uvar_pack.end(), pack + vp[m], pack + vp[m + 1]);
@@ -386,11 +392,12 @@ static int build_shared_tables(hc_system *s)
         for (int m = 0; m < nmon; m++)
             if (uid[m] >= 0) uuse[fill[uid[m]]++] = m;
     }
-    // one device block: uvar_ptr | uvar_pack | uuse_ptr | uuse | term_row | cptr | cterm
+    // one device block: uvar_ptr | uvar_pack | uuse_ptr | uuse | term_row | cptr | cterm | ucost
     auto sz = [](size_t n) { return hc_align256(sizeof(int32_t) * (n > 0 ? n : 1)); };
     const size_t o1 = 0, o2 = o1 + sz(uvar_ptr.size()), o3 = o2 + sz(uvar_pack.size()),
                  o4 = o3 + sz(uuse_ptr.size()), o5 = o4 + sz(uuse.size()), o6 = o5 + sz(term_row.size()),
-                 o7 = o6 + sz(cptr.size()), total = o7 + sz(cterm.size());
+                 o7 = o6 + sz(cptr.size()), o8 = o7 + sz(cterm.size()),
+                 total = o8 + hc_align256(sizeof(double) * ucost.size());
     cudaError_t e = cudaMalloc(&s->dev_shared, total);
     if (e != cudaSuccess) return hc_cuda_fail(e, "cudaMalloc(shared tables)");
     char *b = (char *)s->dev_shared;
@@ -405,6 +412,8 @@ static int build_shared_tables(hc_system *s)
     put(o5, term_row);
     put(o6, cptr);
     put(o7, cterm);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + o8, ucost.data(), sizeof(double) * ucost.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return hc_cuda_fail(e, "cudaMemcpy(shared tables)");
     DevSys &d = s->dev;
     d.nuniq = nuniq;
@@ -415,6 +424,7 @@ static int build_shared_tables(hc_system *s)
     d.term_row = (const int32_t *)(b + o5);
     d.cptr = (const int32_t *)(b + o6);
     d.cterm = (const int32_t *)(b + o7);
+    d.ucost = (const double *)(b + o8);
     s->ops_term = ops_term;
     s->ops_shared = ops_shared;
     // the shared scheme when it saves at least a tenth of the FP64 instructions
