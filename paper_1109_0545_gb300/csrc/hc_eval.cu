@@ -32,9 +32,12 @@ template void launch_powers<2>(int, int, int, int, const double *, double *, cud
 template void launch_powers<4>(int, int, int, int, const double *, double *, cudaStream_t);
 
 // Persistent warps over tasks (32-point tile, group of rows); the row groups of one tile
-// are consecutive tasks, so the warps of a block share their points' data in L1.
+// are consecutive tasks, so the warps of a block share their points' data in L1.  In
+// quad double the register budget is that of four 128-thread blocks per SM (128
+// registers; 40 bytes of spills): the warps' FP64 chains need the fourth block's warps
+// to hide their latency.
 template <int L, bool JAC>
-__global__ void __launch_bounds__(128, L == 4 ? 3 : 1) k_eval_pts(DevSys S, int npts, double t,
+__global__ void __launch_bounds__(128, L == 4 ? 4 : 1) k_eval_pts(DevSys S, int npts, double t,
                                                   const double *__restrict__ X,
                                                   const double *__restrict__ PW,
                                                   double *__restrict__ F, double *__restrict__ J,
