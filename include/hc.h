@@ -100,7 +100,11 @@ int hc_system_info(const hc_system *sys, int *n, int *npoly, int *nmon, int *nva
  *           and every d_i >= 1).
  *   x  device X[2][L][n][npts];  f  device F[2][L][npoly][npts];
  *   J  device J[2][L][npoly][n][npts], or NULL for values only.
- * Uses the system's workspace (allocated on first use, grown as needed).
+ * Uses the system's workspace (allocated on first use, grown as needed): the power table
+ * and, in the shared-monomial scheme when npts / 32 tiles give the GPU fewer than about 8
+ * warps per SM, the partial sums of G groups of distinct monomials (G up to 64:
+ * G * 2 * L * npoly * (1 + n) doubles per point, about 2 GB in all for Table 1's
+ * 40 x 40 system in DD, whatever npts).
  * npts == 0 is a no-op.  Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA.
  */
 int hc_eval_jac(hc_system *sys, int npts, double t, const double *x, double *f, double *J,
@@ -121,6 +125,7 @@ int hc_eval_jac(hc_system *sys, int npts, double t, const double *x, double *f, 
  *   status   device int32[npts]: HC_OK, HC_SINGULAR (x unchanged) or HC_NONFINITE
  *            (x unchanged)
  *   sweeps   device int32[npts] (may be NULL): refinement sweeps taken (0 for native)
+ * Uses the system's workspace: that of hc_eval_jac plus h, J and the solve's arrays.
  * Errors: HC_EINVAL, HC_ENOMEM, HC_ECUDA.
  */
 int hc_newton_step(hc_system *sys, int npts, double t, double *x, int lu_mode,
