@@ -362,6 +362,9 @@ def hc_set_tiles(rows_per_task: int, blocks_per_sm: int) -> None:
 
 def hc_set_track_tiles(threads_per_block: int = 0, blocks_per_sm: int = 0, factors: int = 0,
                        grid_chunk: int = 0) -> None:
+    """Execution shape of the tracker for later calls (0 = automatic): threads per path
+    block (64, 128, 256; 512 in double and double-double), path blocks per SM, FP64 factors
+    in shared (0, 1) or global (2) memory, and the whole-GPU engine's chunk length."""
     _check("hc_set_track_tiles", load().hc_set_track_tiles(int(threads_per_block), int(blocks_per_sm),
                                                            int(factors), int(grid_chunk)))
 
