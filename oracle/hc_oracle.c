@@ -33,10 +33,12 @@
  * Pins (tests/test_oracle_pins.py, tests/test_oracle_tracker_pins.py) tie each routine to
  * exact rationals, sympy, mpmath or closed forms: the predictors to exact polynomial
  * interpolation, the tracker to homotopies whose paths are exactly linear or quadratic
- * in t, the homotopy at 0 < t < 1 to mpmath.  Parity unpinned: the exact stage-by-stage
- * trajectory of or_track on a general system with n > 1.  Only its invariants (steps on
- * the lambda0 2^-j lattice, accepted steps adding up to 1), its univariate end points,
- * the constructed paths and the start-system roots are pinned.
+ * in t and to decoupled systems whose paths are continued roots in closed form, the
+ * homotopy at 0 < t < 1 to mpmath.  Parity unpinned: the exact stage-by-stage
+ * trajectory (which steps are accepted) of or_track on a general coupled system with
+ * n > 1.  Only its invariants (steps on the lambda0 2^-j lattice, accepted steps adding
+ * up to 1), its univariate end points, the constructed and decoupled paths and the
+ * start-system roots are pinned.
  *
  * Readings of the paper where it is silent or garbled are stated at each routine.
  * Layout of every array here is point-major, array-of-structures:

@@ -15,6 +15,9 @@
   bits, at t whose 1 - t is not a double (a 1 - t rounded to one limb fails).
 * Replay and resume: replaying the accepted t values of a tracked path reproduces its end
   point bit for bit; resuming it in chunks of stages reproduces the one-call run.
+* The tracker on a decoupled system of three unknowns (f_i = x_i^{d_i} - c_i, degrees 2, 3
+  and 4): each coordinate of the path is a d_i-th root continued along t in closed form,
+  and every accepted point, at the t the tracker records, lies on it (mpmath at 200 bits).
 """
 from fractions import Fraction as Fr
 
@@ -305,3 +308,76 @@ def test_resume_in_chunks_equals_one_call():
         (r.status, r.n_succ, r.n_corr, r.newton_its, r.end_its)
     assert stats["t_end"] == r.t_end and stats["res_end"] == r.res_end
     assert np.array_equal(np.concatenate(logs), r.log)
+
+
+def decoupled_system(c, d):
+    """f_i = x_i^{d_i} - c_i, i = 0..n-1: the homotopy decouples, and coordinate i of the
+    path solves x^{d_i} = (gamma (1-t) + t c_i) / (gamma (1-t) + t)."""
+    n = len(c)
+    coef, idx, ex, var_ptr = [], [], [], [0]
+    for i in range(n):
+        coef += [1.0, -c[i]]
+        idx.append(i)
+        ex.append(d[i])
+        var_ptr += [var_ptr[-1] + 1, var_ptr[-1] + 1]
+    return synth.System(n=n, npoly=n, mon_ptr=np.arange(0, 2 * n + 1, 2, dtype=np.int32),
+                        var_ptr=np.array(var_ptr, np.int32), var_idx=np.array(idx, np.int32),
+                        var_exp=np.array(ex, np.int32), coef=np.array(coef, dtype=complex))
+
+
+def exact_branch(gamma, c, d, ts, mpmath):
+    """x(t) along ts (increasing, from 0) for x^d = w(t), continued from x(0) = 1 in
+    substeps of at most 1e-3, each time taking the d-th root nearest the previous point."""
+    G, C = mpmath.mpc(gamma.real, gamma.imag), mpmath.mpc(c.real, c.imag)
+    x, t0, out = mpmath.mpc(1), mpmath.mpf(0), []
+    for t in ts:
+        T = mpmath.mpf(t)
+        m = max(1, int(mpmath.ceil((T - t0) / mpmath.mpf("1e-3"))))
+        for k in range(1, m + 1):
+            s = t0 + (T - t0) * k / m
+            w = (G * (1 - s) + s * C) / (G * (1 - s) + s)
+            r0 = mpmath.root(w, d)
+            roots = [r0 * mpmath.exp(2j * mpmath.pi * q / d) for q in range(d)]
+            x = min(roots, key=lambda r: abs(r - x))
+        t0 = T
+        out.append(x)
+    return out
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_tracker_points_lie_on_the_exact_path_of_a_decoupled_system(L):
+    """n = 3, degrees 2, 3, 4: every accepted point of the oracle's tracker, at the t it
+    records, equals the exact path point (each coordinate a continued d-th root, mpmath at
+    200 bits) to the corrector's accuracy, and the end point equals the root reached at
+    t = 1 within the tolerance of the precision."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 200
+    rng = np.random.default_rng(970 + L)
+    d = [2, 3, 4]
+    c = [synth.unit_complex(rng) for _ in d]
+    gamma = synth.unit_complex(rng)
+    s = decoupled_system(c, d)
+    g = np.array([gamma.real, gamma.imag])
+    eps = {2: 1e-26, 4: 1e-58}[L]
+    o = track_opts(predictor=1, eps=eps, eps_end=eps, eps_end_x=eps)
+    st = oracle.PathState()
+    z = synth.limbs(np.ones(s.n), L)
+    zp, zpp = np.zeros_like(z), np.zeros_like(z)
+    ts, pts = [], []
+    for _ in range(5000):
+        before = st.n_succ
+        st, z, zp, zpp, _, _ = oracle.track_resume(s.as_dict(), s.coef_limbs(L), g, o, st, z, zp, zpp, 1)
+        if st.phase == 3:
+            break
+        if st.n_succ > before:
+            ts.append(st.t)
+            pts.append(z.copy())
+    assert oracle.STATUS[st.status] == "OK" and len(ts) > 10
+    ts.append(1.0)
+    pts.append(z.copy())
+    for i in range(s.n):
+        exact = exact_branch(gamma, c[i], d[i], ts, mpmath)
+        for k, (t, p) in enumerate(zip(ts, pts)):
+            got = mpmath.mpc(sum(mpmath.mpf(float(v)) for v in p[i, 0]), sum(mpmath.mpf(float(v)) for v in p[i, 1]))
+            tol = 1e-12 if k < len(ts) - 1 else {2: 1e-28, 4: 1e-58}[L]
+            assert abs(got - exact[k]) <= tol * max(1, abs(exact[k])), (i, k, t, float(abs(got - exact[k])))
