@@ -444,3 +444,56 @@ def test_track_step_sizes_follow_the_halving_rule():
     assert abs(acc["lam"].sum() - 1.0) < 1e-12
     assert abs(r.n_succ * r.avg_step - 1.0) < 1e-12
     assert r.n_succ == len(acc) and r.n_corr == len(r.log)
+
+
+def _linear_system(A, b):
+    """f_i = sum_j A_ij x_j - b_i as a sparse system (every x_j a monomial of degree 1)."""
+    n = A.shape[0]
+    mon_ptr, var_ptr, idx, ex, coef = [0], [0], [], [], []
+    for i in range(n):
+        for j in range(n):
+            idx.append(j)
+            ex.append(1)
+            var_ptr.append(var_ptr[-1] + 1)
+            coef.append(A[i, j])
+        var_ptr.append(var_ptr[-1])
+        coef.append(-b[i])
+        mon_ptr.append(len(coef))
+    return synth.System(n=n, npoly=n, mon_ptr=np.array(mon_ptr, np.int32), var_ptr=np.array(var_ptr, np.int32),
+                        var_idx=np.array(idx, np.int32), var_exp=np.array(ex, np.int32),
+                        coef=np.array(coef, dtype=complex))
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("log_cond", [6, 12])
+def test_refined_solve_of_an_ill_conditioned_system_reaches_the_working_precision(L, log_cond):
+    """One Newton step from 0 on a linear system f = A x - b is x = A^-1 b.  With A
+    conditioned to 10^6 or 10^12, the FP64 LU gains only 10 or 4 digits a refinement sweep;
+    the mixed solve (and its stop rule: a correction that does not shrink is not applied)
+    must still reach the exact solution (mpmath at 400 bits) to within cond x the precision,
+    as the native elimination in the working precision does."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 400
+    rng = np.random.default_rng(990 + L + log_cond)
+    n = 4
+    q1, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    q2, _ = np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    A = q1 @ np.diag(np.logspace(0, -log_cond, n)) @ q2
+    b = rng.normal(size=n) + 1j * rng.normal(size=n)
+    s = _linear_system(A, b)
+    Am = mpmath.matrix([[mpmath.mpc(A[i, j].real, A[i, j].imag) for j in range(n)] for i in range(n)])
+    bm = mpmath.matrix([mpmath.mpc(v.real, v.imag) for v in b])
+    xm = mpmath.lu_solve(Am, bm)
+    xnorm = max(abs(xm[i]) for i in range(n))
+    x0 = np.zeros((1, n, 2, L))
+    bound = 100 * 10.0 ** log_cond * 2.0 ** (-52 * L)
+    for lu_mode, refine in ((0, 1), (1, 64)):
+        x1, _, st, sw = oracle.newton_step(s.as_dict(), s.coef_limbs(L), x0, -1.0, np.array([1.0, 0.0]),
+                                           lu_mode, refine)
+        assert st[0] == 0
+        got = [mpmath.mpc(sum(mpmath.mpf(float(v)) for v in x1[0, i, 0]),
+                          sum(mpmath.mpf(float(v)) for v in x1[0, i, 1])) for i in range(n)]
+        err = max(abs(got[i] - xm[i]) for i in range(n)) / xnorm
+        assert err <= bound, (lu_mode, L, log_cond, float(err), int(sw[0]))
+        if lu_mode == 1:
+            assert 1 <= sw[0] < 64   # the refinement stopped by itself
