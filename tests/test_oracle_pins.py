@@ -497,3 +497,21 @@ def test_refined_solve_of_an_ill_conditioned_system_reaches_the_working_precisio
         assert err <= bound, (lu_mode, L, log_cond, float(err), int(sw[0]))
         if lu_mode == 1:
             assert 1 <= sw[0] < 64   # the refinement stopped by itself
+
+
+def test_paths_of_a_system_without_finite_roots_do_not_end_ok():
+    """f_1 = x_1 x_2 - 1, f_2 = x_1 x_2 - 2 has no finite root, while the total-degree start
+    system has 4: every path from a start root goes to infinity, so none may end as OK;
+    each stops as DIVERGED (|x| above the bound) or MIN_STEP (the step collapsed near the
+    end), with |x| far above its start."""
+    s = synth.System(n=2, npoly=2, mon_ptr=np.array([0, 2, 4], np.int32),
+                     var_ptr=np.array([0, 2, 2, 4, 4], np.int32), var_idx=np.array([0, 1, 0, 1], np.int32),
+                     var_exp=np.array([1, 1, 1, 1], np.int32), coef=np.array([1, -1, 1, -2], dtype=complex))
+    g = synth.unit_complex(np.random.default_rng(1010))
+    for a in (1.0, -1.0):
+        for b in (1.0, -1.0):
+            x0 = synth.limbs(np.array([a, b], dtype=complex), 2)
+            r = oracle.track(s.as_dict(), s.coef_limbs(2), x0, np.array([g.real, g.imag]), default_opts())
+            assert oracle.STATUS[r.status] in ("DIVERGED", "MIN_STEP"), (a, b, oracle.STATUS[r.status])
+            xmax = max(abs(complex(r.x[j, 0, 0], r.x[j, 1, 0])) for j in range(2))
+            assert xmax > 10.0, (a, b, xmax)
