@@ -515,3 +515,60 @@ def test_paths_of_a_system_without_finite_roots_do_not_end_ok():
             assert oracle.STATUS[r.status] in ("DIVERGED", "MIN_STEP"), (a, b, oracle.STATUS[r.status])
             xmax = max(abs(complex(r.x[j, 0, 0], r.x[j, 1, 0])) for j in range(2))
             assert xmax > 10.0, (a, b, xmax)
+
+
+def test_eval_at_high_degree_matches_mpmath():
+    """The shapes the parity tests need the oracle for at high degree: 8 rows of Table 1's
+    common-support system (degree up to 80, up to 32 variables a monomial) and monomials
+    of exponent 64, at torus points: DD and QD within 1e-28 / 1e-58 of mpmath at 400 bits,
+    normwise over a point's values and over its Jacobian."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 400
+    full, _ = synth.common_support_system(1)
+    rows = list(range(8))
+    mon_ptr, var_ptr, idx, ex, coef = [0], [0], [], [], []
+    for i in rows:
+        for m in range(full.mon_ptr[i], full.mon_ptr[i + 1]):
+            q0, q1 = full.var_ptr[m], full.var_ptr[m + 1]
+            idx.extend(full.var_idx[q0:q1])
+            ex.extend(full.var_exp[q0:q1])
+            var_ptr.append(var_ptr[-1] + q1 - q0)
+            coef.append(full.coef[m])
+        mon_ptr.append(len(coef))
+    # and one row of exponent-64 monomials
+    for vs in ([0, 5], [31], [3, 7, 11]):
+        idx.extend(vs)
+        ex.extend([64] * len(vs))
+        var_ptr.append(var_ptr[-1] + len(vs))
+        coef.append(np.exp(1j * len(vs)))
+    mon_ptr.append(len(coef))
+    s = synth.System(n=full.n, npoly=len(rows) + 1, mon_ptr=np.array(mon_ptr, np.int32),
+                     var_ptr=np.array(var_ptr, np.int32), var_idx=np.array(idx, np.int32),
+                     var_exp=np.array(ex, np.int32), coef=np.array(coef))
+    assert int(s.var_exp.max()) == 64 and max(np.diff(s.var_ptr)) >= 20
+    xs = synth.torus_points(np.random.default_rng(1020), 2, s.n)
+    for L, tol in ((2, 1e-28), (4, 1e-58)):
+        f, J, _ = oracle.evaluate(s.as_dict(), s.coef_limbs(L), synth.limbs(xs, L), mode=1)
+        for p in range(2):
+            X = [mpmath.mpc(float(z.real), float(z.imag)) for z in xs[p]]
+            fe, Je = [], []
+            for i in range(s.npoly):
+                fi = mpmath.mpc(0)
+                Ji = [mpmath.mpc(0)] * s.n
+                for m in range(s.mon_ptr[i], s.mon_ptr[i + 1]):
+                    term = mpmath.mpc(float(s.coef[m].real), float(s.coef[m].imag))
+                    vs = list(range(s.var_ptr[m], s.var_ptr[m + 1]))
+                    for q in vs:
+                        term *= X[s.var_idx[q]] ** int(s.var_exp[q])
+                    fi += term
+                    for q in vs:
+                        Ji[s.var_idx[q]] += term * int(s.var_exp[q]) / X[s.var_idx[q]]
+                fe.append(fi)
+                Je.append(Ji)
+
+            def val(a):
+                return mpmath.mpc(sum(mpmath.mpf(float(v)) for v in a[0]), sum(mpmath.mpf(float(v)) for v in a[1]))
+            fscale = max(abs(v) for v in fe)
+            jscale = max(abs(v) for row in Je for v in row)
+            assert max(abs(val(f[p, i]) - fe[i]) for i in range(s.npoly)) <= tol * fscale
+            assert max(abs(val(J[p, i, j]) - Je[i][j]) for i in range(s.npoly) for j in range(s.n)) <= tol * jscale
